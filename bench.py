@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the length-bucketed word sort on GB300.
+
+One step = the whole path (bucket by length -> per-bucket sort -> gather) over
+the 16,777,216-word pre-tokenised table (32-byte records, lengths 1..32,
+30 % Zipf words), the largest single-GPU workload.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--alg auto|merge|odd_even] [--words N]
+
+N > 1 runs under torchrun as independent replicas (one full workload per
+GPU; the path has no exchange step), value = all words sorted / slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mwords/s sorted end-to-end (tokenise/bucket/sort/gather)"
+WORKLOAD = "large: 16,777,216 pre-tokenised words, W=32, seed 2"
+N_WORDS = 16_777_216
+W = 32
+SEED = 2
+
+# dram bytes per launch from the committed ncu summaries (profiles/), by kernel;
+# None where no capture of the current kernel exists yet.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--alg", default="auto")
+    ap.add_argument("--words", type=int, default=N_WORDS)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_bytes(hist: np.ndarray, n: int, Wd: int, tile: int) -> dict:
+    """Algorithmic bytes of one step, per kernel, from the length histogram.
+
+    Elements are (ceil(L/8) uint64 keys, uint32 index)."""
+    L = np.arange(hist.size)
+    K = (L + 7) // 8
+    elem = (8 * K + 4) * hist  # bytes of all elements of each bucket
+    kb = {
+        "hist": n,                                            # read len
+        "scatter": n * (Wd + 1) + int(elem.sum()),            # read rec+len, write keys+idx
+        "tile_bitonic": 2 * int(elem.sum()),                  # read + write every element
+        "tile_odd_even": 2 * int(elem.sum()),
+        "gather": int(elem.sum()) + n * (Wd + 4),             # read keys+idx, write rec+perm
+    }
+    merge = 0
+    R = tile
+    while R < n:
+        merge += 2 * int(elem[hist > R].sum())
+        R *= 2
+    kb["merge_pass"] = merge
+    return kb
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1411_5283_gb300 as bs
+    from paper_1411_5283_gb300 import synth
+
+    bs._lib.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = args.words
+    rec_np, len_np = synth.large_records(SEED, n, W)
+    rec_h = torch.from_numpy(rec_np).pin_memory()
+    len_h = torch.from_numpy(len_np).pin_memory()
+    rec = rec_h.to(dev)
+    ln = len_h.to(dev)
+    s = bs.Sorter(n, W, device=str(dev))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.sort_records(rec, ln, n, alg=args.alg)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = s.status()
+    if st != 0:
+        raise RuntimeError(f"device status {bs.bsort_status_string(st)}")
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    bs.bsort_profile_reset()
+    bs.bsort_profile_enable(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    bs.bsort_profile_enable(False)
+    prof = bs.bsort_profile_read()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    out_rec_h = torch.empty((n, W), dtype=torch.uint8).pin_memory()
+    out_perm_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    off_h = torch.empty(W + 2, dtype=torch.int32).pin_memory()
+    k2 = args.e2e_steps or max(3, min(args.steps, 10))
+
+    def e2e_step():
+        rec.copy_(rec_h, non_blocking=True)
+        ln.copy_(len_h, non_blocking=True)
+        s.sort_records(rec, ln, n, alg=args.alg)
+        out_rec_h.copy_(s.out_rec[:n], non_blocking=True)
+        out_perm_h.copy_(s.out_perm[:n], non_blocking=True)
+        off_h.copy_(s.off, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0.record(stream)
+    for _ in range(k2):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / k2
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    off = s.off.cpu().numpy().view(np.uint32).astype(np.int64)
+    hist = np.diff(off)[: W + 1]  # hist[L] = words of length L (index 0 empty)
+    hist = np.concatenate([[0], hist[1:]]) if hist.size else hist
+    tile = 2048 if args.alg != "odd_even" else 512
+    kb = kernel_bytes(hist, n, W, tile)
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 1.0))
+    name, (launches, tot_ms) = dom
+    steps_prof = args.steps
+    bytes_step = kb.get(name, 0)
+    ms_step_kernel = tot_ms / steps_prof
+    achieved = bytes_step / (ms_step_kernel * 1e-3) / 1e9 if ms_step_kernel > 0 else 0.0
+    peak, peak_kind = peaks()
+    compulsory = n * (W + 1) + n * (W + 4)
+    path_gbs = compulsory / (ms * 1e-3) / 1e9
+    return {
+        "ms": ms, "e2e_ms": e2e_ms, "n": n, "prof": prof, "clk": clk,
+        "roofline": {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": NCU_TRAFFIC.get(name), "peak_kind": peak_kind,
+                     "launches_per_step": launches / steps_prof,
+                     "algorithmic_bytes_per_step": bytes_step},
+        "path_roofline": {"compulsory_bytes_per_word": W + 1 + W + 4,
+                          "achieved": round(path_gbs, 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(path_gbs / peak, 4)},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "h2d": n * (W + 1), "d2h": n * (W + 4) + 4 * (W + 2),
+    }
+
+
+def cpu_baseline(budget_s: float = 20.0):
+    """The oracle, as it stands, on bounded samples of the same workload."""
+    import oracle
+    from paper_1411_5283_gb300 import synth
+    oracle.build()
+    rec, ln = synth.large_records(SEED, 1 << 20, W)
+    out = {}
+    # the paper's method (bubble sort per length) on a 65,536-word sample
+    m = 65_536
+    t0 = time.perf_counter()
+    res = oracle.bubble_sort(oracle.Words(rec[:m], ln[:m]))
+    tb = time.perf_counter() - t0
+    assert res.status == 0
+    out["bubble"] = (m, tb)
+    # the stable-sort formulation on a 1,048,576-word sample
+    t0 = time.perf_counter()
+    res = oracle.stable_sort(oracle.Words(rec, ln))
+    ts = time.perf_counter() - t0
+    assert res.status == 0
+    out["stable"] = (rec.shape[0], ts)
+    return {"value": round(m / tb / 1e6, 6), "unit": "Mwords/s", "cores": 1, "kind": "oracle",
+            "sample": f"bubble sort per length (paper's method) on the first {m:,} words of the "
+                      f"workload: {tb:.2f} s; stable-sort oracle on the first "
+                      f"{rec.shape[0]:,} words: {ts:.2f} s = "
+                      f"{rec.shape[0] / ts / 1e6:.3f} Mwords/s",
+            "stable_sort_mwords_s": round(rec.shape[0] / ts / 1e6, 4)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores (bounded sample per step)."""
+    import oracle
+    from paper_1411_5283_gb300 import synth
+    oracle.build()
+    m = 65_536
+    rec, ln = synth.large_records(SEED, m, W)
+    w = oracle.Words(rec, ln)
+    for _ in range(args.warmup):
+        oracle.bubble_sort(w)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.bubble_sort(w)
+        times.append(time.perf_counter() - t0)
+        assert r.status == 0
+    sec = sum(times) / len(times)
+    v = m / sec / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Mwords/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_words": m, "algorithm": "bubble sort",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Mwords/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"bubble sort per length on the first {m:,} words of "
+                                       f"the workload, per step"},
+            "e2e": {"value": round(v, 6), "unit": "Mwords/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        n_total = r["n"] * world
+        value = n_total / (r["ms"] * 1e-3) / 1e6
+        e2e_value = n_total / (r["e2e_ms"] * 1e-3) / 1e6
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mwords/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "words": r["n"], "W": W, "alg": args.alg,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs (553 MB) larger than L2 (129 MB); no flush"},
+            "e2e": {"value": round(e2e_value, 2), "unit": "Mwords/s",
+                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+            "roofline": r["roofline"],
+            "path_roofline": r["path_roofline"],
+            "gpu_launches": r["gpu_launches"],
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in r["prof"].items()},
+            "clocks": r["clk"],
+        }
+        line["cpu_baseline"] = cpu_baseline() if world == 1 else None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * bsort.h -- C ABI of the GB300 (sm_103a) length-bucketed word sort.
+ *
+ * The method (Alyasseri et al., arXiv 1411.5283, §3 Methodology,
+ * "Pre-processing"): strip the special characters from a text (phase 1), put
+ * the words into sub-arrays by character count with shorter lengths first
+ * (phase 2; the abstract sizes each sub-array by the number of words of that
+ * length), and sort every sub-array alphabetically (phase 3) with bubble sort
+ * (§2, §3.2) or merge sort (§4 "MPI Implementation", §5: chunks sorted
+ * separately, then merged).  The result is every word ordered by
+ * (length, bytes), equal words in input order.
+ *
+ * Conventions shared by every call
+ *  - All pointers named d_* are device pointers owned by the caller.  The
+ *    library allocates nothing on these paths; scratch lives in a caller-owned
+ *    workspace of bsort_workspace_size() bytes (256-byte aligned).  Prepare a
+ *    new workspace once with bsort_workspace_init().  Where things live inside
+ *    the workspace depends only on (ws_bytes, W), so pass the same ws_bytes
+ *    and W to every call that shares a workspace.
+ *  - Record arrays (d_rec, d_out_rec) must be 16-byte aligned.
+ *  - All calls are asynchronous on stream s and return synchronously only
+ *    argument errors (BSORT_E_INVALID, BSORT_E_WORKSPACE, BSORT_E_CAPACITY
+ *    for host-visible sizes) or a launch failure (BSORT_E_CUDA).
+ *  - Errors found by the kernels (a word longer than W, more words than the
+ *    capacity, a zero length) are recorded in a sticky status word inside the
+ *    workspace; read it with bsort_get_status(), clear it with
+ *    bsort_reset_status().  When several errors occur, the smallest code is
+ *    reported.  Kernels never trap; after an error the outputs are undefined
+ *    but every access stays inside the buffers described here.
+ *  - W is the record width in bytes: 8, 16, 24 or 32.  A word is at most W
+ *    letters.  Word lengths L run 1..W.
+ *  - Records are W bytes, the word's letters first, zero padded.  Bytes after
+ *    the word's length are ignored on input and written as zero on output.
+ *  - Indices are uint32: at most 2^32 - 2 words per call.
+ *  - Buckets: off[] has W + 2 entries; off[L] is the number of words shorter
+ *    than L (off[0] = off[1] = 0, off[W+1] = n).  Bucket L occupies output
+ *    ranks off[L] .. off[L+1]-1.
+ */
+#ifndef BSORT_H_
+#define BSORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSORT_OK = 0,
+  BSORT_E_INVALID = 1,        /* bad argument, or a record of length 0       */
+  BSORT_E_WORD_TOO_LONG = 2,  /* a word has more than W letters              */
+  BSORT_E_CAPACITY = 3,       /* more words than max_words / list capacity   */
+  BSORT_E_WORKSPACE = 4,      /* workspace missing, misaligned or too small  */
+  BSORT_E_CUDA = 5,           /* a CUDA launch or copy failed                */
+  BSORT_E_TIMEOUT = 6,        /* a bounded device-side wait gave up          */
+  BSORT_E_NOMEM = 7           /* serving admission: not enough device memory */
+} bsort_status;
+
+/* Per-bucket sort algorithm (third phase of §3 "Pre-processing").
+ *  BSORT_ODD_EVEN: odd-even transposition sort of shared-memory tiles (the
+ *    data-parallel form of the paper's bubble sort, §2), then merge-path
+ *    merging of the sorted tiles (the paper's merge of sorted chunks, §4).
+ *  BSORT_MERGE:    bitonic-network sort of shared-memory tiles, then
+ *    merge-path merging.
+ *  BSORT_AUTO:     the fastest available strategy for the sizes at hand.
+ * Every algorithm gives byte-identical output. */
+typedef enum { BSORT_ODD_EVEN = 0, BSORT_MERGE = 1, BSORT_AUTO = 2 } bsort_alg;
+
+/* Tuning knobs; a field of 0 takes the library default.  Results never
+ * depend on them.
+ *  tile               elements per bitonic tile (power of two, 256..4096)
+ *  oddeven_max        elements per odd-even tile (power of two, 64..2048)
+ *  threads_per_bucket threads per tile-sort CTA (128, 256, 512 or 1024)
+ *  merge_fanin        elements per merge-path partition (power of two, 512..4096) */
+typedef struct {
+  uint32_t tile, oddeven_max, threads_per_bucket, merge_fanin;
+} bsort_tune;
+
+/* One list of a batched call (bsort_sort_many).
+ *  text_off, text_bytes  byte range of the list's text (text mode only)
+ *  word_off              first record of the list in the concatenated word
+ *                        arrays (input records in record mode; output records,
+ *                        output permutation in both modes)
+ *  n_words               number of words (record mode; ignored in text mode)
+ *  max_words             capacity of the list's output slots (text mode: the
+ *                        most words the text may hold; record mode: >= n_words) */
+typedef struct {
+  uint64_t text_off, text_bytes;
+  uint64_t word_off;
+  uint32_t n_words, max_words;
+} bsort_list;
+
+/* Bytes of workspace for up to max_words words of width W with algorithm alg
+ * (every call below that takes d_ws needs this many bytes; 0 if the arguments
+ * are invalid). */
+size_t bsort_workspace_size(uint64_t max_words, uint32_t W, bsort_alg alg);
+
+/* Number of words a workspace of ws_bytes bytes holds for width W (the
+ * inverse of bsort_workspace_size; 0 if W is invalid). */
+uint64_t bsort_workspace_capacity(size_t ws_bytes, uint32_t W);
+
+/* Zeroes the workspace header (status word and counters).  Call once on a new
+ * workspace before first use. */
+bsort_status bsort_workspace_init(void* d_ws, size_t ws_bytes, cudaStream_t s);
+
+/* Phase 1 (§3 "Pre-processing", first phase): splits text into words.
+ * A letter is an ASCII byte 'A'..'Z' or 'a'..'z'; every other byte separates
+ * words (so "don't" is "don", "t").  Words are numbered in order of
+ * appearance.  Writes, for word i < max_words: d_rec[i*W .. i*W+W-1] (zero
+ * padded), d_len[i] and d_src_off[i] (offset of its first byte in the text).
+ * *d_n_words receives min(words found, max_words).  n_bytes must be below
+ * 2^32.  Device errors: BSORT_E_WORD_TOO_LONG, BSORT_E_CAPACITY.
+ * Workspace: bsort_workspace_size(max_words, W, alg) for any alg. */
+bsort_status bsort_tokenize(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                            uint32_t max_words, uint8_t* d_rec, uint8_t* d_len,
+                            uint32_t* d_src_off, uint32_t* d_n_words, void* d_ws,
+                            size_t ws_bytes, cudaStream_t s);
+
+/* Phase 2 (§3 "Pre-processing", second phase; abstract): groups the n words
+ * d_rec[n*W], d_len[n] into buckets by length, shorter first, each bucket in
+ * input order (a stable scatter), and packs each word into ceil(L/8)
+ * big-endian uint64 keys inside the workspace, so that comparing keys as
+ * integers compares the words byte by byte.  Writes d_off[W+2].
+ * Device errors: BSORT_E_INVALID (a length of 0), BSORT_E_WORD_TOO_LONG
+ * (a length above W); such words are left out of every bucket. */
+bsort_status bsort_bucket_by_length(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                    uint32_t W, uint32_t* d_off, void* d_ws, size_t ws_bytes,
+                                    cudaStream_t s);
+
+/* Phase 3 (§3 "Pre-processing", third phase; §2; §4-§5): sorts every bucket
+ * left in the workspace by bsort_bucket_by_length, by the words' bytes and
+ * then by input index, with algorithm alg (tune may be NULL).  n, W and d_off
+ * must be those given to / written by bsort_bucket_by_length. */
+bsort_status bsort_sort_buckets(uint32_t n, uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                const uint32_t* d_off, void* d_ws, size_t ws_bytes,
+                                cudaStream_t s);
+
+/* Concatenation in ascending length (§3, second phase "shorter before
+ * longer"): writes the sorted words d_out_rec[n*W] (zero padded, rebuilt from
+ * the packed keys) and d_out_perm[n] (input index of each output word). */
+bsort_status bsort_gather(uint32_t n, uint32_t W, const uint32_t* d_off, const void* d_ws,
+                          size_t ws_bytes, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                          cudaStream_t s);
+
+/* Phases 2-3 and the concatenation in one call on a word table (the same
+ * result as bucket_by_length + sort_buckets + gather).  Resets the status
+ * word first. */
+bsort_status bsort_sort_records(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                uint8_t* d_out_rec, uint32_t* d_out_perm, uint32_t* d_off,
+                                void* d_ws, size_t ws_bytes, cudaStream_t s);
+
+/* Phases 1-3 and the concatenation in one call on raw text.  The word count
+ * stays on the device (*d_n_words); nothing is copied to the host.  Resets
+ * the status word first.  d_out_perm[r] is the input index (order of
+ * appearance) of output word r; d_src_off[i] the text offset of word i. */
+bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                             uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                             uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                             uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                             uint32_t* d_off, void* d_ws, size_t ws_bytes, cudaStream_t s);
+
+/* Copies the bucket contents left in the workspace by bsort_bucket_by_length
+ * or bsort_sort_buckets (for inspection and tests): d_keys[k*n + r] is key
+ * word k of bucket position r (0 beyond the word's ceil(L/8) keys),
+ * d_idx[r] its input index. */
+bsort_status bsort_export_buckets(uint32_t n, uint32_t W, const uint32_t* d_off,
+                                  const void* d_ws, size_t ws_bytes, uint64_t* d_keys,
+                                  uint32_t* d_idx, cudaStream_t s);
+
+/* Per-kernel device timing (tracing; off by default).  While enabled, every
+ * kernel launch of the library is bracketed by two CUDA events on its stream.
+ * bsort_profile_read() waits for them and returns the number of distinct
+ * kernels seen since the last reset; for entry i (i < max_entries) it writes
+ * the launch count, the summed device milliseconds and the kernel name
+ * (NUL-separated, packed into names[names_bytes]).  Host-side, thread-safe. */
+bsort_status bsort_profile_enable(int on);
+bsort_status bsort_profile_reset(void);
+uint32_t bsort_profile_read(char* names, size_t names_bytes, uint64_t* launches, double* ms,
+                            uint32_t max_entries);
+
+/* Synchronises s and returns the smallest device-detected error recorded in
+ * the workspace since the last reset (BSORT_OK if none). */
+bsort_status bsort_get_status(const void* d_ws, cudaStream_t s);
+
+/* Clears the workspace status word (asynchronously on s). */
+bsort_status bsort_reset_status(void* d_ws, cudaStream_t s);
+
+/* Human-readable name of a status code. */
+const char* bsort_status_string(bsort_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSORT_H_ */

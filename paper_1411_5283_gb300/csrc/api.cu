@@ -1,0 +1,199 @@
+// C ABI of the bsort library: argument checks, workspace views and launches.
+// Every operation runs in the kernels of this directory; nothing here touches
+// the data.
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace bsort;
+
+namespace {
+
+bool valid_W(uint32_t W) { return W >= 8 && W <= kMaxW && W % 8 == 0; }
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+bsort_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BSORT_OK : BSORT_E_CUDA; }
+
+bsort_status check_ws(const void* d_ws, size_t ws_bytes, uint32_t W, uint64_t need_words) {
+  if (!d_ws || !aligned(d_ws, 256)) return BSORT_E_WORKSPACE;
+  if (ws_capacity(ws_bytes, W) < need_words) return BSORT_E_WORKSPACE;
+  return BSORT_OK;
+}
+
+// Resolves the algorithm and tuning knobs; returns false on an invalid knob.
+bool resolve(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
+  bsort_tune t{};
+  if (tune) t = *tune;
+  const uint32_t KW = W / 8;
+  p->alg = alg == BSORT_ODD_EVEN ? BSORT_ODD_EVEN : BSORT_MERGE;
+  if (p->alg == BSORT_ODD_EVEN) {
+    p->tile = t.oddeven_max ? t.oddeven_max : 512;
+    if (!pow2(p->tile) || p->tile < 64 || p->tile > 2048) return false;
+  } else {
+    p->tile = t.tile ? t.tile : 2048;
+    if (!pow2(p->tile) || p->tile < 256 || p->tile > 4096) return false;
+  }
+  p->threads = t.threads_per_bucket ? t.threads_per_bucket : 256;
+  if (p->threads < 64 || p->threads > 1024 || p->threads % 32) return false;
+  p->part = t.merge_fanin ? t.merge_fanin : (KW >= 3 ? 1024u : 2048u);
+  if (!pow2(p->part) || p->part < 256 || p->part > 4096) return false;
+  if (2ull * p->part * (8 * KW + 4) > 200 * 1024) return false;  // merge CTA shared memory
+  if (p->part > 2 * p->tile) p->part = 2 * p->tile;  // a partition never spans two run pairs
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bsort_workspace_size(uint64_t max_words, uint32_t W, bsort_alg alg) {
+  (void)alg;
+  if (!valid_W(W) || max_words > 0xFFFFFFFEull) return 0;
+  return ws_layout(max_words, W).total;
+}
+
+uint64_t bsort_workspace_capacity(size_t ws_bytes, uint32_t W) {
+  if (!valid_W(W)) return 0;
+  return ws_capacity(ws_bytes, W);
+}
+
+bsort_status bsort_workspace_init(void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  if (!d_ws || !aligned(d_ws, 256) || ws_bytes < sizeof(WsHeader)) return BSORT_E_WORKSPACE;
+  return cuda_status(cudaMemsetAsync(d_ws, 0, 4096, s));
+}
+
+bsort_status bsort_reset_status(void* d_ws, cudaStream_t s) {
+  if (!d_ws || !aligned(d_ws, 256)) return BSORT_E_WORKSPACE;
+  return cuda_status(cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s));
+}
+
+bsort_status bsort_get_status(const void* d_ws, cudaStream_t s) {
+  if (!d_ws || !aligned(d_ws, 256)) return BSORT_E_WORKSPACE;
+  uint32_t flags = 0;
+  if (cudaMemcpyAsync(&flags, d_ws, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return BSORT_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BSORT_E_CUDA;
+  for (int c = 1; c < 32; ++c)
+    if (flags & (1u << c)) return static_cast<bsort_status>(c);
+  return BSORT_OK;
+}
+
+const char* bsort_status_string(bsort_status st) {
+  switch (st) {
+    case BSORT_OK: return "ok";
+    case BSORT_E_INVALID: return "invalid argument";
+    case BSORT_E_WORD_TOO_LONG: return "word longer than the record width";
+    case BSORT_E_CAPACITY: return "more words than the capacity";
+    case BSORT_E_WORKSPACE: return "workspace missing, misaligned or too small";
+    case BSORT_E_CUDA: return "CUDA error";
+    case BSORT_E_TIMEOUT: return "device-side wait timed out";
+    case BSORT_E_NOMEM: return "not enough device memory";
+  }
+  return "unknown status";
+}
+
+bsort_status bsort_tokenize(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                            uint32_t max_words, uint8_t* d_rec, uint8_t* d_len,
+                            uint32_t* d_src_off, uint32_t* d_n_words, void* d_ws,
+                            size_t ws_bytes, cudaStream_t s) {
+  if (!valid_W(W) || n_bytes > 0xFFFF0000ull || (n_bytes && !d_text)) return BSORT_E_INVALID;
+  if (max_words > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (max_words && (!d_rec || !d_len || !d_src_off || !aligned(d_rec, 16))) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, 0)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  return cuda_status(launch_tokenize(d_text, static_cast<uint32_t>(n_bytes), W, max_words, d_rec,
+                                     d_len, d_src_off, d_n_words, ws, s));
+}
+
+bsort_status bsort_bucket_by_length(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                    uint32_t W, uint32_t* d_off, void* d_ws, size_t ws_bytes,
+                                    cudaStream_t s) {
+  if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (n && (!d_rec || !d_len || !aligned(d_rec, 16))) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, n)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  return cuda_status(launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s));
+}
+
+bsort_status bsort_sort_buckets(uint32_t n, uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                const uint32_t* d_off, void* d_ws, size_t ws_bytes,
+                                cudaStream_t s) {
+  if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
+  SortParams p;
+  if (!resolve(alg, tune, W, &p)) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, n)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  return cuda_status(launch_sort(n, W, p, d_off, ws, s));
+}
+
+bsort_status bsort_gather(uint32_t n, uint32_t W, const uint32_t* d_off, const void* d_ws,
+                          size_t ws_bytes, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                          cudaStream_t s) {
+  if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (n && (!d_out_rec || !d_out_perm || !aligned(d_out_rec, 16))) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, n)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  return cuda_status(launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s));
+}
+
+bsort_status bsort_sort_records(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                uint8_t* d_out_rec, uint32_t* d_out_perm, uint32_t* d_off,
+                                void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (n && (!d_rec || !d_len || !d_out_rec || !d_out_perm)) return BSORT_E_INVALID;
+  if (n && (!aligned(d_rec, 16) || !aligned(d_out_rec, 16))) return BSORT_E_INVALID;
+  if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
+  SortParams p;
+  if (!resolve(alg, tune, W, &p)) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, n)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BSORT_E_CUDA;
+  cudaError_t e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
+  if (e == cudaSuccess) e = launch_sort(n, W, p, d_off, ws, s);
+  if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
+  return cuda_status(e);
+}
+
+bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                             uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                             uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                             uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                             uint32_t* d_off, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  if (!valid_W(W) || n_bytes > 0xFFFF0000ull || (n_bytes && !d_text) || !d_off || !d_n_words)
+    return BSORT_E_INVALID;
+  if (max_words > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (max_words && (!d_rec || !d_len || !d_src_off || !d_out_rec || !d_out_perm))
+    return BSORT_E_INVALID;
+  if (max_words && (!aligned(d_rec, 16) || !aligned(d_out_rec, 16))) return BSORT_E_INVALID;
+  if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
+  SortParams p;
+  if (!resolve(alg, tune, W, &p)) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, max_words)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BSORT_E_CUDA;
+  cudaError_t e = launch_tokenize(d_text, static_cast<uint32_t>(n_bytes), W, max_words, d_rec,
+                                  d_len, d_src_off, d_n_words, ws, s);
+  if (e == cudaSuccess) e = launch_bucket(d_rec, d_len, max_words, d_n_words, W, d_off, ws, s);
+  if (e == cudaSuccess) e = launch_sort(max_words, W, p, d_off, ws, s);
+  if (e == cudaSuccess)
+    e = launch_gather(max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
+  return cuda_status(e);
+}
+
+bsort_status bsort_export_buckets(uint32_t n, uint32_t W, const uint32_t* d_off,
+                                  const void* d_ws, size_t ws_bytes, uint64_t* d_keys,
+                                  uint32_t* d_idx, cudaStream_t s) {
+  if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
+  if (n && (!d_keys || !d_idx)) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, n)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  return cuda_status(launch_export(n, W, d_off, ws, d_keys, d_idx, s));
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Shared device helpers and the workspace layout of the bsort library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bsort.h"
+
+namespace bsort {
+
+constexpr uint32_t kMaxW = 32;          // widest record (bytes)
+constexpr uint32_t kMaxK = kMaxW / 8;   // most uint64 key words per word
+constexpr uint32_t kBins = kMaxW + 1;   // length bins 0..W (0 stays empty)
+constexpr uint32_t kHistBlocksMax = 2048;  // blocks of the histogram / scatter grid
+constexpr uint32_t kTextBlocksMax = 4096;  // blocks of the tokeniser grid
+constexpr uint32_t kScanThreads = 1024;
+constexpr uint32_t kSpinLimit = 1u << 26;  // bound on every device-side wait loop
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+// [header 4 KB][block table][keys A][keys B][idx A][idx B][misc]
+// keys X: kK planes of `cap` uint64 (plane k at k*cap); idx X: `cap` uint32.
+// Bucket L occupies positions off[L]..off[L+1]-1 of every plane.
+struct WsHeader {
+  uint32_t status_flags;            // bit c set: error code c was seen
+  uint32_t n_words;                 // device-side word count of the last tokenise
+  uint32_t final_buf[kMaxW + 2];    // per bucket: 0 = sorted data in A, 1 = in B
+  uint32_t tile;                    // tile size used by the last sort
+  uint32_t magic;
+  uint32_t counters[16];            // work-queue counters of persistent kernels
+};
+static_assert(sizeof(WsHeader) <= 4096, "header too large");
+
+constexpr uint32_t kWsMagic = 0x42534f52u;
+
+struct WsLayout {
+  size_t header, table, keys_a, keys_b, idx_a, idx_b, misc, total;
+  uint64_t cap;       // element capacity of each plane (>= max_words + 64)
+  uint32_t K;         // key planes
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout for a plane capacity of `cap` elements (a multiple of 64).
+inline WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
+  WsLayout l{};
+  l.K = W / 8;
+  l.cap = cap;
+  size_t o = 0;
+  l.header = o;  o += 4096;
+  l.table = o;   o += align_up(sizeof(uint32_t) * (size_t)kBins * kHistBlocksMax * 2 + 64 * 1024, 256);
+  l.keys_a = o;  o += align_up(8 * l.cap * l.K, 256);
+  l.keys_b = o;  o += align_up(8 * l.cap * l.K, 256);
+  l.idx_a = o;   o += align_up(4 * l.cap, 256);
+  l.idx_b = o;   o += align_up(4 * l.cap, 256);
+  l.misc = o;    o += 64 * 1024;
+  l.total = o;
+  return l;
+}
+
+// Smallest layout holding max_words words (64 elements of slack per plane).
+inline WsLayout ws_layout(uint64_t max_words, uint32_t W) {
+  return ws_layout_cap(align_up(max_words + 64, 64), W);
+}
+
+// The layout is a pure function of (ws_bytes, W): the largest capacity that
+// fits, so every call on the same workspace agrees on where things live.
+inline WsLayout ws_layout_bytes(size_t ws_bytes, uint32_t W) {
+  const uint32_t K = W / 8;
+  const size_t fixed = ws_layout_cap(0, W).total;
+  if (ws_bytes <= fixed) return ws_layout_cap(0, W);
+  uint64_t cap = (ws_bytes - fixed) / (16ull * K + 8ull) / 64 * 64;
+  while (cap > 0 && ws_layout_cap(cap, W).total > ws_bytes) cap -= 64;
+  return ws_layout_cap(cap, W);
+}
+
+// Words a workspace of ws_bytes can hold.
+inline uint64_t ws_capacity(size_t ws_bytes, uint32_t W) {
+  const uint64_t cap = ws_layout_bytes(ws_bytes, W).cap;
+  return cap > 64 ? cap - 64 : 0;
+}
+
+// Device-side view of the workspace.
+struct Ws {
+  WsHeader* hdr;
+  uint32_t* table;
+  uint64_t* keys[2];
+  uint32_t* idx[2];
+  uint64_t cap;
+  uint32_t K;
+};
+
+inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
+  WsLayout l = ws_layout_bytes(ws_bytes, W);
+  char* b = static_cast<char*>(const_cast<void*>(base));
+  Ws w;
+  w.hdr = reinterpret_cast<WsHeader*>(b + l.header);
+  w.table = reinterpret_cast<uint32_t*>(b + l.table);
+  w.keys[0] = reinterpret_cast<uint64_t*>(b + l.keys_a);
+  w.keys[1] = reinterpret_cast<uint64_t*>(b + l.keys_b);
+  w.idx[0] = reinterpret_cast<uint32_t*>(b + l.idx_a);
+  w.idx[1] = reinterpret_cast<uint32_t*>(b + l.idx_b);
+  w.cap = l.cap;
+  w.K = l.K;
+  return w;
+}
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (host).
+// `current` remembers the limit already set for that kernel.
+template <typename Kernel>
+inline cudaError_t ensure_smem(Kernel k, size_t bytes, size_t* current) {
+  if (bytes <= 48 * 1024 || bytes <= *current) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess) *current = bytes;
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_error(WsHeader* h, int code) {
+  atomicOr(&h->status_flags, 1u << code);
+}
+
+__device__ __forceinline__ bool is_letter(uint32_t b) {
+  return ((b | 0x20u) - 'a') < 26u;
+}
+
+// Byte-reverses a uint64 so that the first byte in memory becomes the most
+// significant: integer order of the result is lexicographic byte order.
+__device__ __forceinline__ uint64_t bswap64(uint64_t x) {
+  uint32_t lo = static_cast<uint32_t>(x), hi = static_cast<uint32_t>(x >> 32);
+  uint32_t nlo = __byte_perm(hi, 0, 0x0123), nhi = __byte_perm(lo, 0, 0x0123);
+  return (static_cast<uint64_t>(nhi) << 32) | nlo;
+}
+
+// Big-endian key word k of a word of length L: keeps its bytes 8k..min(L,8k+8)-1.
+__device__ __forceinline__ uint64_t key_mask(uint32_t L, uint32_t k) {
+  int c = static_cast<int>(L) - static_cast<int>(8 * k);
+  if (c <= 0) return 0ull;
+  if (c >= 8) return ~0ull;
+  return ~0ull << (64 - 8 * c);
+}
+
+__device__ __forceinline__ uint32_t keys_for_len(uint32_t L) { return (L + 7) >> 3; }
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Element of a bucket: K key words then the input index; a strict total order.
+template <int K>
+struct Elem {
+  uint64_t k[K];
+  uint32_t idx;
+};
+
+template <int K>
+__device__ __forceinline__ bool elem_less(const Elem<K>& a, const Elem<K>& b) {
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (a.k[i] != b.k[i]) return a.k[i] < b.k[i];
+  return a.idx < b.idx;
+}
+
+// Shared-memory structure-of-arrays tile: planes of keys then idx.
+template <int K>
+struct SmemTile {
+  uint64_t* k[K];
+  uint32_t* idx;
+  __device__ __forceinline__ Elem<K> get(uint32_t i) const {
+    Elem<K> e;
+#pragma unroll
+    for (int j = 0; j < K; ++j) e.k[j] = k[j][i];
+    e.idx = idx[i];
+    return e;
+  }
+  __device__ __forceinline__ void put(uint32_t i, const Elem<K>& e) const {
+#pragma unroll
+    for (int j = 0; j < K; ++j) k[j][i] = e.k[j];
+    idx[i] = e.idx;
+  }
+};
+
+template <int K>
+__device__ __forceinline__ Elem<K> load_elem(const Ws& ws, int buf, uint64_t pos) {
+  Elem<K> e;
+#pragma unroll
+  for (int j = 0; j < K; ++j) e.k[j] = ws.keys[buf][j * ws.cap + pos];
+  e.idx = ws.idx[buf][pos];
+  return e;
+}
+
+template <int K>
+__device__ __forceinline__ void store_elem(const Ws& ws, int buf, uint64_t pos, const Elem<K>& e) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) ws.keys[buf][j * ws.cap + pos] = e.k[j];
+  ws.idx[buf][pos] = e.idx;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy (TMA engine) staging of global ranges into shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared; dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier; gives up after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+}  // namespace bsort

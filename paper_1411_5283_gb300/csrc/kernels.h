@@ -1,0 +1,62 @@
+// Host-side launchers of the bsort kernels (one translation unit each).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bsort {
+
+// Per-kernel event timing (profile.cu); no-ops unless bsort_profile_enable(1).
+bool profiling();
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(cudaStream_t s);
+
+// Launches `kernel<<<grid, block, smem, s>>>(args...)` bracketed by profile events.
+#define BSORT_LAUNCH(name, kernel, grid, block, smem, s, ...) \
+  do {                                                        \
+    ::bsort::prof_begin(name, s);                             \
+    kernel<<<grid, block, smem, s>>>(__VA_ARGS__);            \
+    ::bsort::prof_end(s);                                     \
+  } while (0)
+
+// Geometry of the histogram / scatter grid: block b owns words [b*wpb, (b+1)*wpb).
+struct HistGeom {
+  uint32_t wpb, G;
+};
+HistGeom hist_geom(uint32_t n_cap);
+
+// In-place exclusive scan of data[0..n) on one block; *total receives the sum.
+void launch_scan(uint32_t* data, uint32_t n, uint32_t* total, cudaStream_t s);
+
+cudaError_t launch_tokenize(const uint8_t* text, uint32_t n_bytes, uint32_t W, uint32_t max_words,
+                            uint8_t* rec, uint8_t* len, uint32_t* src_off, uint32_t* d_n_words,
+                            const Ws& ws, cudaStream_t s);
+
+// Phase 2: histogram, scan, stable scatter + key packing into keys/idx A.
+// d_n (nullable) holds the word count on the device; n_cap bounds it.
+cudaError_t launch_bucket(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
+                          const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
+                          cudaStream_t s);
+
+struct SortParams {
+  int alg;             // bsort_alg (resolved: ODD_EVEN or MERGE)
+  uint32_t tile;       // elements per tile
+  uint32_t threads;    // threads per tile-sort CTA
+  uint32_t part;       // elements per merge-path partition
+};
+
+// Phase 3: tile sort of every bucket, then merge passes until each bucket is
+// one run.  n_cap bounds the word count (sizes the grids).
+cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const uint32_t* d_off,
+                        const Ws& ws, cudaStream_t s);
+
+// Concatenation: sorted records (from the keys) and the permutation.
+cudaError_t launch_gather(uint32_t n_cap, const uint32_t* d_n, uint32_t W, const uint32_t* d_off,
+                          const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
+
+cudaError_t launch_export(uint32_t n, uint32_t W, const uint32_t* d_off, const Ws& ws,
+                          uint64_t* keys, uint32_t* idx, cudaStream_t s);
+
+}  // namespace bsort

@@ -1,0 +1,127 @@
+// Phase 3 of the method (§3 Methodology, "Pre-processing", third phase):
+// every length bucket is sorted alphabetically.
+//
+// The paper sorts each sub-array with bubble sort (§2, §3.2) and, under MPI,
+// has every process bubble-sort one chunk before the master merges the sorted
+// chunks (§4 "MPI Implementation", §5).  The GPU form keeps that shape:
+//   tile_sort_kernel   one CTA per tile of a bucket; the tile is staged into
+//                      shared memory by the bulk-copy (TMA) engine and sorted
+//                      by odd-even transposition (bubble sort's data-parallel
+//                      form: alternate even / odd neighbour exchanges, stop
+//                      after an even and an odd phase without exchange) or by
+//                      a bitonic network;
+//   merge_pass_kernel  merge-path merging of neighbouring sorted runs, run
+//                      length doubling each pass, until each bucket is one run.
+// Elements are (key words..., input index); comparing the tuple is a strict
+// total order, so every algorithm and tile size gives the same result.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "sort_impl.cuh"
+
+namespace bsort {
+
+namespace {
+
+// Tiles of bucket L are numbered from the prefix sum of ceil(cnt_L / T) over
+// shorter lengths.
+__device__ TileRef find_tile(const uint32_t* s_off, uint32_t W, uint32_t T, uint32_t t) {
+  TileRef r{0, 0, 0, false};
+  uint32_t acc = 0;
+  for (uint32_t L = 1; L <= W; ++L) {
+    const uint32_t cnt = s_off[L + 1] - s_off[L];
+    const uint32_t nt = (cnt + T - 1) / T;
+    if (t < acc + nt) {
+      r.L = L;
+      r.start = s_off[L] + (t - acc) * T;
+      r.len = min(T, s_off[L + 1] - r.start);
+      r.valid = true;
+      return r;
+    }
+    acc += nt;
+  }
+  return r;
+}
+
+__global__ void tile_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t T,
+                                 uint32_t part, int odd_even, Ws ws) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint32_t s_off[kMaxW + 2];
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x <= W + 1) {
+    // record where each bucket's sorted run ends up after the merge passes
+    const uint32_t L = threadIdx.x;
+    const uint32_t cnt = (L >= 1 && L <= W) ? s_off[L + 1] - s_off[L] : 0u;
+    ws.hdr->final_buf[L] = merge_passes(cnt, T) & 1u;
+    if (L == 0) ws.hdr->tile = T;
+  }
+  const TileRef tr = find_tile(s_off, W, T, blockIdx.x);
+  if (!tr.valid) return;
+  uint8_t* sm = align128(smem);
+  switch (keys_for_len(tr.L)) {
+    case 1: sort_one_tile<1>(sm, T, tr, odd_even, ws); break;
+    case 2: sort_one_tile<2>(sm, T, tr, odd_even, ws); break;
+    case 3: sort_one_tile<3>(sm, T, tr, odd_even, ws); break;
+    default: sort_one_tile<4>(sm, T, tr, odd_even, ws); break;
+  }
+}
+
+// One merge pass over every bucket longer than R: partition `part`-sized
+// output ranges of each bucket; CTA -> (bucket, partition) by prefix sums.
+__global__ void merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R,
+                                  uint32_t part, int src, Ws ws) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint32_t s_off[kMaxW + 2];
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  uint32_t acc = 0, L = 0, o0 = 0;
+  for (uint32_t l = 1; l <= W; ++l) {
+    const uint32_t cnt = s_off[l + 1] - s_off[l];
+    if (cnt <= R) continue;
+    const uint32_t np = (cnt + part - 1) / part;
+    if (blockIdx.x < acc + np) {
+      L = l;
+      o0 = (blockIdx.x - acc) * part;
+      break;
+    }
+    acc += np;
+  }
+  if (L == 0) return;
+  const uint32_t bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
+  switch (keys_for_len(L)) {
+    case 1: merge_partition<1>(smem, part, bstart, cnt, R, o0, src, ws); break;
+    case 2: merge_partition<2>(smem, part, bstart, cnt, R, o0, src, ws); break;
+    case 3: merge_partition<3>(smem, part, bstart, cnt, R, o0, src, ws); break;
+    default: merge_partition<4>(smem, part, bstart, cnt, R, o0, src, ws); break;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const uint32_t* d_off,
+                        const Ws& ws, cudaStream_t s) {
+  const uint32_t KW = W / 8;
+  const uint32_t T = p.tile;
+  const size_t tsm = tile_smem_bytes(KW, T);
+  static size_t tile_smem_set = 0, merge_smem_set = 0;
+  const uint32_t part = p.part;
+  const size_t msm = merge_smem_bytes(KW, part);
+  cudaError_t e = ensure_smem(tile_sort_kernel, tsm, &tile_smem_set);
+  if (e == cudaSuccess) e = ensure_smem(merge_pass_kernel, msm, &merge_smem_set);
+  if (e != cudaSuccess) return e;
+  const uint32_t tiles = (n_cap + T - 1) / T + W;
+  BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "tile_odd_even" : "tile_bitonic", tile_sort_kernel, tiles,
+               p.threads, tsm, s, d_off, W, T, p.part, p.alg == BSORT_ODD_EVEN ? 1 : 0, ws);
+  const uint32_t parts = (n_cap + part - 1) / part + W;
+  int src = 0;
+  for (uint64_t R = T; R < n_cap; R <<= 1) {
+    BSORT_LAUNCH("merge_pass", merge_pass_kernel, parts, 256, msm, s, d_off, W,
+                 static_cast<uint32_t>(R), part, src, ws);
+    src ^= 1;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bsort

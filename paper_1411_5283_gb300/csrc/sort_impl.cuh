@@ -1,0 +1,202 @@
+// Device building blocks of phase 3 (§3 Methodology, "Pre-processing", third
+// phase; §2 bubble sort; §4-§5 merge of sorted chunks), shared by the single-list
+// and the batched pipelines: shared-memory tile sorts (odd-even transposition
+// and bitonic) staged by the bulk-copy engine, and merge-path merging.
+#pragma once
+
+#include "common.cuh"
+
+namespace bsort {
+
+// Which tile of which bucket a CTA owns.
+struct TileRef {
+  uint32_t L, start, len;
+  bool valid;
+};
+
+__device__ __forceinline__ uint32_t merge_passes(uint32_t cnt, uint32_t T) {
+  uint32_t p = 0;
+  for (uint64_t R = T; cnt > R; R <<= 1) ++p;
+  return p;
+}
+
+template <int K>
+__device__ void bitonic_tile(const SmemTile<K>& t, uint32_t len) {
+  uint32_t Tp = 2;
+  while (Tp < len) Tp <<= 1;
+  Elem<K> inf;
+#pragma unroll
+  for (int j = 0; j < K; ++j) inf.k[j] = ~0ull;
+  inf.idx = ~0u;
+  for (uint32_t i = len + threadIdx.x; i < Tp; i += blockDim.x) t.put(i, inf);
+  __syncthreads();
+  for (uint32_t k = 2; k <= Tp; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t p = threadIdx.x; p < Tp / 2; p += blockDim.x) {
+        const uint32_t lo = 2 * j * (p / j) + (p % j);
+        const uint32_t hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const Elem<K> a = t.get(lo), b = t.get(hi);
+        if (elem_less(b, a) == up) {
+          t.put(lo, b);
+          t.put(hi, a);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Odd-even transposition sort: phase ph compares pairs (2p + ph%2, 2p + ph%2 + 1)
+// and exchanges those out of order; after an even and an odd phase in a row
+// without exchange every neighbour pair is ordered.  At most len phases.
+template <int K>
+__device__ void odd_even_tile(const SmemTile<K>& t, uint32_t len) {
+  bool prev_quiet = false;
+  for (uint32_t ph = 0; ph < len; ++ph) {
+    const uint32_t s = ph & 1u;
+    int swapped = 0;
+    for (uint32_t p = threadIdx.x; 2 * p + s + 1 < len; p += blockDim.x) {
+      const uint32_t lo = 2 * p + s;
+      const Elem<K> a = t.get(lo), b = t.get(lo + 1);
+      if (elem_less(b, a)) {
+        t.put(lo, b);
+        t.put(lo + 1, a);
+        swapped = 1;
+      }
+    }
+    const bool quiet = __syncthreads_or(swapped) == 0;
+    if (quiet && prev_quiet) break;
+    prev_quiet = quiet;
+  }
+}
+
+// Shared memory of a tile-sort CTA: [mbarrier 16 B][KW key planes of T+2][idx T+4],
+// plus 128 bytes of slack to align the start.
+__host__ __device__ inline size_t tile_smem_bytes(uint32_t KW, uint32_t T) {
+  return 128 + 16 + static_cast<size_t>(KW) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
+}
+
+__device__ __forceinline__ uint8_t* align128(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+}
+
+template <int K>
+__device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool odd_even,
+                              const Ws& ws) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* kplane = reinterpret_cast<uint64_t*>(smem + 16);
+  uint32_t* iplane = reinterpret_cast<uint32_t*>(smem + 16 + static_cast<size_t>(K) * (T + 2) * 8);
+  // 16-byte aligned source ranges covering [start, start + len)
+  const uint32_t ks = tr.start & ~1u, is = tr.start & ~3u;
+  const uint32_t kbytes = ((tr.start + tr.len - ks) * 8 + 15) & ~15u;
+  const uint32_t ibytes = ((tr.start + tr.len - is) * 4 + 15) & ~15u;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, K * kbytes + ibytes);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      bulk_g2s(kplane + j * (T + 2), ws.keys[0] + j * ws.cap + ks, kbytes, bar);
+    bulk_g2s(iplane, ws.idx[0] + is, ibytes, bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0) {
+      set_error(ws.hdr, BSORT_E_TIMEOUT);
+      mbar_wait_bounded(bar, 0);  // let copies in flight land before the CTA exits
+    }
+    return;
+  }
+  SmemTile<K> t;
+#pragma unroll
+  for (int j = 0; j < K; ++j) t.k[j] = kplane + j * (T + 2) + (tr.start - ks);
+  t.idx = iplane + (tr.start - is);
+  if (odd_even)
+    odd_even_tile<K>(t, tr.len);
+  else
+    bitonic_tile<K>(t, tr.len);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tr.len; i += blockDim.x)
+    store_elem<K>(ws, 0, tr.start + i, t.get(i));
+}
+
+// ---------------------------------------------------------------------------
+// Merge path
+// ---------------------------------------------------------------------------
+
+// Number of elements of A among the first `diag` outputs of merge(A, B).
+template <int K, typename GetA, typename GetB>
+__device__ uint32_t merge_path(GetA A, uint32_t na, GetB B, uint32_t nb, uint32_t diag) {
+  uint32_t lo = diag > nb ? diag - nb : 0u;
+  uint32_t hi = min(diag, na);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (elem_less<K>(A(mid), B(diag - 1 - mid)))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Shared memory of a merge CTA: input then output, each part x (8 KW + 4) bytes.
+__host__ __device__ inline size_t merge_smem_bytes(uint32_t KW, uint32_t part) {
+  return 2 * static_cast<size_t>(part) * (8 * KW + 4);
+}
+
+template <int K>
+__device__ void merge_partition(uint8_t* smem, uint32_t part, uint32_t bstart, uint32_t cnt,
+                                uint32_t R, uint32_t o0, int src, const Ws& ws) {
+  __shared__ uint32_t s_split[2];
+  const uint32_t o1 = min(o0 + part, cnt);
+  const uint32_t ps = o0 / (2 * R) * (2 * R);
+  const uint32_t na = min(R, cnt - ps);
+  const uint32_t nb = min(R, cnt - ps - na);
+  const uint32_t a0 = bstart + ps, b0 = a0 + na;
+  auto gA = [&](uint32_t i) { return load_elem<K>(ws, src, a0 + i); };
+  auto gB = [&](uint32_t i) { return load_elem<K>(ws, src, b0 + i); };
+  if (threadIdx.x < 2) {
+    const uint32_t d = (threadIdx.x == 0 ? o0 : o1) - ps;
+    s_split[threadIdx.x] = merge_path<K>(gA, na, gB, nb, d);
+  }
+  __syncthreads();
+  const uint32_t i0 = s_split[0], i1 = s_split[1];
+  const uint32_t j0 = (o0 - ps) - i0, j1 = (o1 - ps) - i1;
+  const uint32_t ca = i1 - i0, cb = j1 - j0, tot = ca + cb;
+  // smem: input tile (A part then B part), output tile
+  SmemTile<K> in, out;
+  uint64_t* kp = reinterpret_cast<uint64_t*>(smem);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    in.k[j] = kp + j * part;
+    out.k[j] = kp + (K + j) * part;
+  }
+  in.idx = reinterpret_cast<uint32_t*>(kp + 2 * K * part);
+  out.idx = in.idx + part;
+  for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x)
+    in.put(i, i < ca ? gA(i0 + i) : gB(j0 + i - ca));
+  __syncthreads();
+  const uint32_t per = (part + blockDim.x - 1) / blockDim.x;
+  const uint32_t d0 = min(tot, threadIdx.x * per), d1 = min(tot, d0 + per);
+  auto sA = [&](uint32_t i) { return in.get(i); };
+  auto sB = [&](uint32_t i) { return in.get(ca + i); };
+  uint32_t ia = merge_path<K>(sA, ca, sB, cb, d0);
+  uint32_t ib = d0 - ia;
+  for (uint32_t d = d0; d < d1; ++d) {
+    bool takeA;
+    if (ia >= ca) takeA = false;
+    else if (ib >= cb) takeA = true;
+    else takeA = elem_less<K>(in.get(ia), in.get(ca + ib));
+    out.put(d, takeA ? in.get(ia++) : in.get(ca + ib++));
+  }
+  __syncthreads();
+  const int dst = src ^ 1;
+  for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x)
+    store_elem<K>(ws, dst, bstart + o0 + i, out.get(i));
+}
+
+}  // namespace bsort
