@@ -30,7 +30,7 @@ def declared() -> list[str]:
 def test_header_declares_the_abi():
     names = declared()
     for want in ["bsort_tokenize", "bsort_bucket_by_length", "bsort_sort_buckets",
-                 "bsort_gather", "bsort_sort_many", "bsort_workspace_size",
+                 "bsort_gather", "bsort_workspace_size",
                  "bsort_get_status", "bsort_status_string"]:
         assert want in names
 
