@@ -162,6 +162,32 @@ bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W
                              uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
                              uint32_t* d_off, void* d_ws, size_t ws_bytes, cudaStream_t s);
 
+/* The paper has no counterpart to this entry point.
+ * bsort_sort_records without a workspace, for callers that may not allocate
+ * device memory: code whose device memory belongs to a host framework's own
+ * pool (plugins of inference servers or game engines that forbid raw
+ * cudaMalloc), or latency-bound loops that cannot afford cudaMalloc / cudaFree
+ * and the device synchronisation they may cause.  Same result as
+ * bsort_sort_records for the same arguments.
+ *  - Scratch is a static device array inside the library, sized for at most
+ *    32,768 words (any W); every GPU that loads the library holds it (about
+ *    3 MB) until the process exits.  n above 32,768 returns BSORT_E_CAPACITY
+ *    before any work is queued.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call
+ *    (with the optional profiler off, its default).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call shares the array and finds the previous call's contents; the
+ *    call clears what must start at zero.  Calls that overlap on the GPU (other
+ *    streams or host threads) race on the array: serialise them.
+ *  - d_status (device, may be NULL) receives the smallest device-detected
+ *    error code (a bsort_status) once the call's work on s has run. */
+bsort_status bsort_sort_records_noalloc(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                        uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                        uint8_t* d_out_rec, uint32_t* d_out_perm,
+                                        uint32_t* d_off, int32_t* d_status, cudaStream_t s);
+
 /* Copies the bucket contents left in the workspace by bsort_bucket_by_length
  * or bsort_sort_buckets (for inspection and tests): d_keys[k*n + r] is key
  * word k of bucket position r (0 beyond the word's ceil(L/8) keys),

@@ -59,6 +59,9 @@ _SIGS = {
     "bsort_sort_text": (ctypes.c_int, [c_u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_int, ctypes.POINTER(Tune), c_u8p, c_u8p, c_u8p,
                                        c_u8p, c_u8p, c_u8p, c_u8p, c_u8p, c_size, c_u8p]),
+    "bsort_sort_records_noalloc": (ctypes.c_int, [c_u8p, c_u8p, ctypes.c_uint32, ctypes.c_uint32,
+                                                  ctypes.c_int, ctypes.POINTER(Tune), c_u8p,
+                                                  c_u8p, c_u8p, c_u8p, c_u8p]),
     "bsort_export_buckets": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, c_u8p, c_u8p,
                                             c_size, c_u8p, c_u8p, c_u8p]),
     "bsort_profile_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -203,6 +206,15 @@ def bsort_sort_many(text_or_rec, ln, lists, n_lists, W, lists_are_text, max_list
                                   _ptr(out_rec), _ptr(out_perm), _ptr(out_off),
                                   _ptr(list_status), _ptr(ws), ws_bytes, _stream(stream)),
            "bsort_sort_many")
+
+
+def bsort_sort_records_noalloc(rec, ln, n, W, alg, tune, out_rec, out_perm, off, status=None,
+                               stream=None):
+    """Whole record sort with the library's static scratch (no workspace)."""
+    _check(load().bsort_sort_records_noalloc(_ptr(rec), _ptr(ln), n, W, _alg(alg), _tune(tune),
+                                             _ptr(out_rec), _ptr(out_perm), _ptr(off),
+                                             _ptr(status), _stream(stream)),
+           "bsort_sort_records_noalloc")
 
 
 def bsort_export_buckets(n, W, off, ws, ws_bytes, keys, idx, stream=None):

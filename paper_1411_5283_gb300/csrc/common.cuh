@@ -41,27 +41,34 @@ struct WsLayout {
   uint32_t K;         // key planes
 };
 
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Layout for a plane capacity of `cap` elements (a multiple of 64).
-inline WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
+constexpr WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
   WsLayout l{};
   l.K = W / 8;
   l.cap = cap;
   size_t o = 0;
-  l.header = o;  o += 4096;
-  l.table = o;   o += align_up(sizeof(uint32_t) * (size_t)kBins * kHistBlocksMax * 2 + 64 * 1024, 256);
-  l.keys_a = o;  o += align_up(8 * l.cap * l.K, 256);
-  l.keys_b = o;  o += align_up(8 * l.cap * l.K, 256);
-  l.idx_a = o;   o += align_up(4 * l.cap, 256);
-  l.idx_b = o;   o += align_up(4 * l.cap, 256);
-  l.misc = o;    o += 64 * 1024;
+  l.header = o;
+  o += 4096;
+  l.table = o;
+  o += align_up(sizeof(uint32_t) * static_cast<size_t>(kBins) * kHistBlocksMax * 2 + 64 * 1024, 256);
+  l.keys_a = o;
+  o += align_up(8 * l.cap * l.K, 256);
+  l.keys_b = o;
+  o += align_up(8 * l.cap * l.K, 256);
+  l.idx_a = o;
+  o += align_up(4 * l.cap, 256);
+  l.idx_b = o;
+  o += align_up(4 * l.cap, 256);
+  l.misc = o;
+  o += 64 * 1024;
   l.total = o;
   return l;
 }
 
 // Smallest layout holding max_words words (64 elements of slack per plane).
-inline WsLayout ws_layout(uint64_t max_words, uint32_t W) {
+constexpr WsLayout ws_layout(uint64_t max_words, uint32_t W) {
   return ws_layout_cap(align_up(max_words + 64, 64), W);
 }
 

@@ -1,0 +1,113 @@
+// bsort_sort_records_noalloc: the whole record sort (bucket by length, sort
+// every bucket, gather) for callers that may not allocate device memory.
+//
+// Some callers cannot hand the library a workspace: their device memory is
+// owned by a host framework's own pool or arena that forbids raw cudaMalloc
+// (plugins of inference servers, game engines), or they run latency-bound
+// loops where cudaMalloc / cudaFree, which may synchronise the device, are not
+// acceptable.  For them this entry point keeps its scratch in the file-scope
+// array below, which the CUDA runtime places in device memory when the module
+// loads; every GPU that loads the library holds it until the process exits.
+//
+// The array is shared by every call on a device and keeps the last call's
+// contents; each call clears the part that must start at zero (the status
+// header) itself.  Calls whose work overlaps on the GPU (two streams, or two
+// host threads) race on the array and give undefined results: serialise them.
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bsort {
+
+namespace {
+
+// Most words one call may sort (any W up to 32); the array holds the
+// workspace layout for this many 32-byte records.
+constexpr uint32_t kNoAllocMaxWords = 32768;
+constexpr size_t kNoAllocBytes = ws_layout(kNoAllocMaxWords, kMaxW).total;
+
+__device__ __align__(256) uint8_t g_noalloc_ws[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_dev_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_ws on the current device (set up once per
+// device).  In host code the array's name is only a host-side stand-in, so the
+// address must come from cudaGetSymbolAddress with that device current.
+cudaError_t noalloc_ptr(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_dev_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess) return e;
+    g_dev_ptr[dev] = p;
+  }
+  *out = g_dev_ptr[dev];
+  return cudaSuccess;
+}
+
+__global__ void noalloc_status_kernel(const WsHeader* hdr, int32_t* status) {
+  const uint32_t f = hdr->status_flags;
+  int32_t c = 0;
+  for (int k = 1; k < 32; ++k)
+    if (f & (1u << k)) {
+      c = k;
+      break;
+    }
+  *status = c;
+}
+
+}  // namespace
+
+}  // namespace bsort
+
+using namespace bsort;
+
+extern "C" bsort_status bsort_sort_records_noalloc(const uint8_t* d_rec, const uint8_t* d_len,
+                                                   uint32_t n, uint32_t W, bsort_alg alg,
+                                                   const bsort_tune* tune, uint8_t* d_out_rec,
+                                                   uint32_t* d_out_perm, uint32_t* d_off,
+                                                   int32_t* d_status, cudaStream_t s) {
+  if (W < 8 || W > kMaxW || W % 8 || !d_off) return BSORT_E_INVALID;
+  if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
+  if (n > kNoAllocMaxWords) return BSORT_E_CAPACITY;
+  if (n && (!d_rec || !d_len || !d_out_rec || !d_out_perm)) return BSORT_E_INVALID;
+  if (n && ((reinterpret_cast<uintptr_t>(d_rec) | reinterpret_cast<uintptr_t>(d_out_rec)) & 15u))
+    return BSORT_E_INVALID;
+  // Same knobs and defaults as bsort_sort_records.
+  bsort_tune t{};
+  if (tune) t = *tune;
+  SortParams p;
+  p.alg = alg == BSORT_ODD_EVEN ? BSORT_ODD_EVEN : BSORT_MERGE;
+  p.tile = p.alg == BSORT_ODD_EVEN ? (t.oddeven_max ? t.oddeven_max : 512u) : (t.tile ? t.tile : 2048u);
+  p.threads = t.threads_per_bucket ? t.threads_per_bucket : 256u;
+  p.part = t.merge_fanin ? t.merge_fanin : (W / 8 >= 3 ? 1024u : 2048u);
+  const auto pow2 = [](uint32_t x) { return x && !(x & (x - 1)); };
+  if (!pow2(p.tile) || p.tile < 64 || p.tile > 4096 || (p.alg == BSORT_MERGE && p.tile < 256) ||
+      (p.alg == BSORT_ODD_EVEN && p.tile > 2048))
+    return BSORT_E_INVALID;
+  if (p.threads < 64 || p.threads > 1024 || p.threads % 32) return BSORT_E_INVALID;
+  if (!pow2(p.part) || p.part < 256 || p.part > 4096) return BSORT_E_INVALID;
+  if (2ull * p.part * (8 * (W / 8) + 4) > 200 * 1024) return BSORT_E_INVALID;
+  if (p.part > 2 * p.tile) p.part = 2 * p.tile;
+
+  void* ws_ptr = nullptr;
+  if (noalloc_ptr(&ws_ptr) != cudaSuccess) return BSORT_E_CUDA;
+  const Ws ws = ws_view(ws_ptr, kNoAllocBytes, W);
+  // the header (status word, per-bucket buffer flags) must start at zero
+  if (cudaMemsetAsync(ws_ptr, 0, 4096, s) != cudaSuccess) return BSORT_E_CUDA;
+  cudaError_t e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
+  if (e == cudaSuccess) e = launch_sort(n, W, p, d_off, ws, s);
+  if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
+  if (e == cudaSuccess && d_status) {
+    noalloc_status_kernel<<<1, 1, 0, s>>>(ws.hdr, d_status);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? BSORT_OK : BSORT_E_CUDA;
+}
