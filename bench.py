@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--alg", default="auto")
     ap.add_argument("--words", type=int, default=N_WORDS)
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="warm-up and timed steps only (for ncu captures): no e2e, no CPU "
+                         "baseline, no clock sampling; prints the device time only")
     return ap.parse_args()
 
 
@@ -120,6 +123,10 @@ def kernel_bytes(hist: np.ndarray, n: int, Wd: int, tile: int) -> dict:
         "tile_bitonic": 2 * int(elem.sum()),                  # read + write every element
         "tile_odd_even": 2 * int(elem.sum()),
         "gather": int(elem.sum()) + n * (Wd + 4),             # read keys+idx, write rec+perm
+        # sample sort: partition reads rec+len and writes elements into segments;
+        # segsort reads the elements and writes the final records + permutation
+        "auto_partition": n * (Wd + 1) + int(elem.sum()),
+        "auto_segsort": int(elem.sum()) + n * (Wd + 4),
     }
     merge = 0
     R = tile
@@ -157,6 +164,18 @@ def run_ours(args, rank, world, local_rank):
     st = s.status()
     if st != 0:
         raise RuntimeError(f"device status {bs.bsort_status_string(st)}")
+
+    if args.profile_run:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "words": n, "alg": args.alg,
+                          "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                          "status": s.status()}), flush=True)
+        return None
 
     # ---- device-resident timed region --------------------------------------
     clocks = Clocks(torch.cuda.current_device())
@@ -317,7 +336,7 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     r = run_ours(args, rank, world, local_rank)
-    if rank == 0:
+    if r is not None and rank == 0:
         n_total = r["n"] * world
         value = n_total / (r["ms"] * 1e-3) / 1e6
         e2e_value = n_total / (r["e2e_ms"] * 1e-3) / 1e6

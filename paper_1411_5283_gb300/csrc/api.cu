@@ -154,7 +154,12 @@ bsort_status bsort_sort_records(const uint8_t* d_rec, const uint8_t* d_len, uint
   if (const bsort_status e = check_ws(d_ws, ws_bytes, W, n)) return e;
   const Ws ws = ws_view(d_ws, ws_bytes, W);
   if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BSORT_E_CUDA;
-  cudaError_t e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
+  cudaError_t e;
+  if (alg == BSORT_AUTO && auto_applies(n, ws, W)) {
+    e = launch_auto(d_rec, d_len, n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
+    return cuda_status(e);
+  }
+  e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
   if (e == cudaSuccess) e = launch_sort(n, W, p, d_off, ws, s);
   if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
   return cuda_status(e);
@@ -179,6 +184,10 @@ bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W
   if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BSORT_E_CUDA;
   cudaError_t e = launch_tokenize(d_text, static_cast<uint32_t>(n_bytes), W, max_words, d_rec,
                                   d_len, d_src_off, d_n_words, ws, s);
+  if (e == cudaSuccess && alg == BSORT_AUTO && auto_applies(max_words, ws, W)) {
+    e = launch_auto(d_rec, d_len, max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
+    return cuda_status(e);
+  }
   if (e == cudaSuccess) e = launch_bucket(d_rec, d_len, max_words, d_n_words, W, d_off, ws, s);
   if (e == cudaSuccess) e = launch_sort(max_words, W, p, d_off, ws, s);
   if (e == cudaSuccess)

@@ -159,9 +159,8 @@ void launch_scan(uint32_t* data, uint32_t n, uint32_t* total, cudaStream_t s) {
   BSORT_LAUNCH("scan", scan_kernel, 1, 1024, 0, s, data, n, total);
 }
 
-cudaError_t launch_bucket(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
-                          const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
-                          cudaStream_t s) {
+cudaError_t launch_hist(const uint8_t* len, uint32_t n_cap, const uint32_t* d_n, uint32_t W,
+                        uint32_t* d_off, const Ws& ws, cudaStream_t s) {
   const HistGeom g = hist_geom(n_cap);
   uint32_t* table = ws.table;
   uint32_t* total = ws.table + kBins * kHistBlocksMax;
@@ -169,6 +168,16 @@ cudaError_t launch_bucket(const uint8_t* rec, const uint8_t* len, uint32_t n_cap
                ws.hdr);
   launch_scan(table, (W + 1) * g.G, total, s);
   BSORT_LAUNCH("offsets", off_kernel, 1, 64, 0, s, table, total, W, g.G, d_off, ws.hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
+                          const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
+                          cudaStream_t s) {
+  const HistGeom g = hist_geom(n_cap);
+  uint32_t* table = ws.table;
+  cudaError_t e = launch_hist(len, n_cap, d_n, W, d_off, ws, s);
+  if (e != cudaSuccess) return e;
   BSORT_LAUNCH("scatter", scatter_kernel, g.G, kThreads, 0, s, rec, len, n_cap, d_n, W, g.wpb,
                g.G, table, ws);
   return cudaGetLastError();

@@ -36,12 +36,47 @@ static_assert(sizeof(WsHeader) <= 4096, "header too large");
 constexpr uint32_t kWsMagic = 0x42534f52u;
 
 struct WsLayout {
-  size_t header, table, keys_a, keys_b, idx_a, idx_b, misc, total;
+  size_t header, table, keys_a, keys_b, keys_c, idx_a, idx_b, idx_c, misc, autoa, total;
   uint64_t cap;       // element capacity of each plane (>= max_words + 64)
   uint32_t K;         // key planes
 };
 
-constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---- sample-sort (AUTO) constants --------------------------------------
+// Per key count K (1..4): shared-memory segment capacity, expected segment
+// size, and the most samples one bucket keeps for choosing its splitters.
+__host__ __device__ constexpr uint32_t auto_seg_cap(uint32_t K) {
+  return K <= 1 ? 8192u : K == 2 ? 4096u : 2048u;
+}
+__host__ __device__ constexpr uint32_t auto_target(uint32_t K) {
+  return auto_seg_cap(K) / 3;  // regions hold 3x the expected count
+}
+__host__ __device__ constexpr uint32_t auto_sample_max(uint32_t K) {
+  return K <= 1 ? 16384u : K == 2 ? 8192u : 4096u;
+}
+constexpr uint32_t kAutoSampleEvery = 32;      // one stratified sample position per 32 words
+constexpr uint32_t kAutoMinWords = 65536;      // smaller inputs take the merge path
+constexpr uint64_t kAutoSlack = 1u << 18;      // extra elements of the third region
+
+__host__ __device__ constexpr uint32_t auto_sample_cap(uint32_t K, uint64_t cap) {
+  return static_cast<uint32_t>(
+      ((auto_sample_max(K) < (cap / 64 < 256 ? 256 : cap / 64)) ? auto_sample_max(K)
+                                                                 : (cap / 64 < 256 ? 256 : cap / 64)) /
+      64 * 64);
+}
+__host__ __device__ constexpr uint64_t auto_max_segments(uint64_t cap) {
+  return cap / 1024 + 2 * kBins + 1;
+}
+constexpr size_t auto_bytes(uint64_t cap, uint32_t W) {
+  size_t samples = 0;
+  for (uint32_t L = 1; L <= W; ++L) {
+    const uint32_t K = (L + 7) / 8;
+    samples += static_cast<size_t>(auto_sample_cap(K, cap)) * (8 * K + 4);
+  }
+  const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 4 * 5 + 8 * 2);
+  return align_up(4096 + samples + tables + 4096, 256);
+}
 
 // Layout for a plane capacity of `cap` elements (a multiple of 64).
 constexpr WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
@@ -57,12 +92,20 @@ constexpr WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
   o += align_up(8 * l.cap * l.K, 256);
   l.keys_b = o;
   o += align_up(8 * l.cap * l.K, 256);
+  // third region: sample-sort room, only in workspaces large enough for it
+  const uint64_t third = cap >= kAutoMinWords + 64 ? cap + kAutoSlack : 0;
+  l.keys_c = o;
+  o += align_up(8 * third * l.K, 256);
   l.idx_a = o;
   o += align_up(4 * l.cap, 256);
   l.idx_b = o;
   o += align_up(4 * l.cap, 256);
+  l.idx_c = o;
+  o += align_up(4 * third, 256);
   l.misc = o;
   o += 64 * 1024;
+  l.autoa = o;
+  o += auto_bytes(cap, W);
   l.total = o;
   return l;
 }
@@ -78,9 +121,14 @@ inline WsLayout ws_layout_bytes(size_t ws_bytes, uint32_t W) {
   const uint32_t K = W / 8;
   const size_t fixed = ws_layout_cap(0, W).total;
   if (ws_bytes <= fixed) return ws_layout_cap(0, W);
-  uint64_t cap = (ws_bytes - fixed) / (16ull * K + 8ull) / 64 * 64;
-  while (cap > 0 && ws_layout_cap(cap, W).total > ws_bytes) cap -= 64;
-  return ws_layout_cap(cap, W);
+  // total(cap) is increasing in cap: binary search the largest cap (a multiple of 64) that fits
+  uint64_t lo = 0, hi = (ws_bytes - fixed) / (16ull * K + 8ull) / 64 + 1;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) / 2;
+    if (ws_layout_cap(mid * 64, W).total <= ws_bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  return ws_layout_cap(lo * 64, W);
 }
 
 // Words a workspace of ws_bytes can hold.
@@ -93,6 +141,7 @@ inline uint64_t ws_capacity(size_t ws_bytes, uint32_t W) {
 struct Ws {
   WsHeader* hdr;
   uint32_t* table;
+  uint8_t* autoa;     // sample-sort area (samples, splitters, segment tables)
   uint64_t* keys[2];
   uint32_t* idx[2];
   uint64_t cap;
@@ -109,6 +158,7 @@ inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
   w.keys[1] = reinterpret_cast<uint64_t*>(b + l.keys_b);
   w.idx[0] = reinterpret_cast<uint32_t*>(b + l.idx_a);
   w.idx[1] = reinterpret_cast<uint32_t*>(b + l.idx_b);
+  w.autoa = reinterpret_cast<uint8_t*>(b + l.autoa);
   w.cap = l.cap;
   w.K = l.K;
   return w;

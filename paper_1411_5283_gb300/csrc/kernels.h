@@ -40,6 +40,18 @@ cudaError_t launch_bucket(const uint8_t* rec, const uint8_t* len, uint32_t n_cap
                           const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
                           cudaStream_t s);
 
+// Phase 2 counts only: histogram, scan, bucket offsets (no scatter).
+cudaError_t launch_hist(const uint8_t* len, uint32_t n_cap, const uint32_t* d_n, uint32_t W,
+                        uint32_t* d_off, const Ws& ws, cudaStream_t s);
+
+// Sample-sort strategy (auto.cu): length totals and bucket offsets (d_off),
+// then the sort; writes the final records and permutation.  auto_applies()
+// says whether the sizes and the workspace suit it.
+bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W);
+cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
+                        const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
+                        uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
+
 struct SortParams {
   int alg;             // bsort_alg (resolved: ODD_EVEN or MERGE)
   uint32_t tile;       // elements per tile

@@ -47,6 +47,51 @@ __device__ void bitonic_tile(const SmemTile<K>& t, uint32_t len) {
   }
 }
 
+// Bitonic sort in the all-ascending form: for each block size k the first
+// step compares element r of a k-block with its mirror k-1-r, the following
+// steps compare i with i + j (j = k/4 .. 1).  Positions at or past n act as
+// +infinity and are never touched, so no padding is written.  Works on shared
+// or global memory (the tile only holds pointers); all threads of the CTA call.
+template <int K>
+__device__ void bitonic_flip(const SmemTile<K>& t, uint32_t n) {
+  if (n < 2) return;
+  uint32_t N = 2, lgN = 1;
+  while (N < n) {
+    N <<= 1;
+    ++lgN;
+  }
+  const uint32_t half = N >> 1;
+  for (uint32_t lk = 1; lk <= lgN; ++lk) {
+    const uint32_t k = 1u << lk, lhk = lk - 1, hk = k >> 1;
+    for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+      const uint32_t blk = p >> lhk, r = p & (hk - 1);
+      const uint32_t lo = (blk << lk) + r, hi = (blk << lk) + (k - 1 - r);
+      if (hi < n) {
+        const Elem<K> a = t.get(lo), b = t.get(hi);
+        if (elem_less(b, a)) {
+          t.put(lo, b);
+          t.put(hi, a);
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t lj = lhk; lj-- > 0;) {
+      const uint32_t j = 1u << lj;
+      for (uint32_t p = threadIdx.x; p < half; p += blockDim.x) {
+        const uint32_t lo = ((p >> lj) << (lj + 1)) + (p & (j - 1)), hi = lo + j;
+        if (hi < n) {
+          const Elem<K> a = t.get(lo), b = t.get(hi);
+          if (elem_less(b, a)) {
+            t.put(lo, b);
+            t.put(hi, a);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Odd-even transposition sort: phase ph compares pairs (2p + ph%2, 2p + ph%2 + 1)
 // and exchanges those out of order; after an even and an odd phase in a row
 // without exchange every neighbour pair is ordered.  At most len phases.
@@ -148,17 +193,20 @@ __host__ __device__ inline size_t merge_smem_bytes(uint32_t KW, uint32_t part) {
   return 2 * static_cast<size_t>(part) * (8 * KW + 4);
 }
 
+// Merges output range [o0, min(o0 + part, cnt)) of one merge pass: runs of
+// length R at src (planes of a bucket or segment, cnt elements) are merged in
+// pairs into dst.  part must divide 2R.  smem holds 2 x part elements.
 template <int K>
-__device__ void merge_partition(uint8_t* smem, uint32_t part, uint32_t bstart, uint32_t cnt,
-                                uint32_t R, uint32_t o0, int src, const Ws& ws) {
+__device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
+                           const SmemTile<K>& dst, uint32_t cnt, uint32_t R, uint32_t o0) {
   __shared__ uint32_t s_split[2];
   const uint32_t o1 = min(o0 + part, cnt);
   const uint32_t ps = o0 / (2 * R) * (2 * R);
   const uint32_t na = min(R, cnt - ps);
   const uint32_t nb = min(R, cnt - ps - na);
-  const uint32_t a0 = bstart + ps, b0 = a0 + na;
-  auto gA = [&](uint32_t i) { return load_elem<K>(ws, src, a0 + i); };
-  auto gB = [&](uint32_t i) { return load_elem<K>(ws, src, b0 + i); };
+  const uint32_t a0 = ps, b0 = ps + na;
+  auto gA = [&](uint32_t i) { return src.get(a0 + i); };
+  auto gB = [&](uint32_t i) { return src.get(b0 + i); };
   if (threadIdx.x < 2) {
     const uint32_t d = (threadIdx.x == 0 ? o0 : o1) - ps;
     s_split[threadIdx.x] = merge_path<K>(gA, na, gB, nb, d);
@@ -194,9 +242,25 @@ __device__ void merge_partition(uint8_t* smem, uint32_t part, uint32_t bstart, u
     out.put(d, takeA ? in.get(ia++) : in.get(ca + ib++));
   }
   __syncthreads();
-  const int dst = src ^ 1;
-  for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x)
-    store_elem<K>(ws, dst, bstart + o0 + i, out.get(i));
+  for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x) dst.put(o0 + i, out.get(i));
+  __syncthreads();  // smem and s_split are reused by the caller's next tile
+}
+
+// Planes of buffer `buf` of the workspace starting at position `start`.
+template <int K>
+__device__ __forceinline__ SmemTile<K> ws_planes(const Ws& ws, int buf, uint64_t start) {
+  SmemTile<K> t;
+#pragma unroll
+  for (int j = 0; j < K; ++j) t.k[j] = ws.keys[buf] + j * ws.cap + start;
+  t.idx = ws.idx[buf] + start;
+  return t;
+}
+
+template <int K>
+__device__ void merge_partition(uint8_t* smem, uint32_t part, uint32_t bstart, uint32_t cnt,
+                                uint32_t R, uint32_t o0, int src, const Ws& ws) {
+  merge_tile<K>(smem, part, ws_planes<K>(ws, src, bstart), ws_planes<K>(ws, src ^ 1, bstart), cnt,
+                R, o0);
 }
 
 }  // namespace bsort
