@@ -40,7 +40,10 @@ namespace {
 
 constexpr uint32_t kPartThreads = 512;
 constexpr uint32_t kSplSmem = 100 * 1024;          // splitter table staged up to this size
-constexpr uint32_t kSegThreads = 1024;
+constexpr uint32_t kSegThreads = 512;
+// One cursor per 128-byte line: the partition's atomics then spread over all
+// L2 slices instead of piling onto the few lines a packed array would use.
+constexpr uint32_t kCursorStride = 32;
 
 // words per lane kept in flight by the partition pass (fewer for wide keys)
 template <int KW> struct PartWords { static constexpr uint32_t value = KW <= 2 ? 4 : 2; };
@@ -62,7 +65,7 @@ struct AutoView {
   uint64_t* samp64;   // per bucket L: K_L planes of sample keys (scap each)
   uint32_t* samp32;   // per bucket L: sample indices
   uint8_t* spl;       // splitter table: per bucket, K_L key planes then indices
-  uint32_t* cursor;   // per segment: slots taken (= exact count after a pass)
+  uint32_t* cursor;   // per segment: slots taken, at cursor[seg * kCursorStride]
   uint32_t* rcap;     // per segment: region capacity (elements)
   uint32_t* outbase;  // per segment: first output rank
   uint32_t* segL;     // per segment: its length bucket
@@ -99,7 +102,7 @@ __host__ __device__ AutoView auto_view(const Ws& ws, uint32_t W) {
   v.ibase = reinterpret_cast<uint64_t*>(p + o);
   o += 8 * G;
   v.cursor = reinterpret_cast<uint32_t*>(p + o);
-  o += 4 * G;
+  o += 4 * G * kCursorStride;
   v.rcap = reinterpret_cast<uint32_t*>(p + o);
   o += 4 * G;
   v.outbase = reinterpret_cast<uint32_t*>(p + o);
@@ -293,7 +296,7 @@ auto_splitter_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws) {
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < p.g; j += blockDim.x) {
     const uint32_t seg = p.seg0 + j;
-    v.cursor[seg] = 0;
+    v.cursor[seg * kCursorStride] = 0;
     v.rcap[seg] = p.cap;
     v.segL[seg] = L;
     v.rbase[seg] = p.r64 + static_cast<uint64_t>(j) * p.cap * p.K;
@@ -311,31 +314,46 @@ auto_splitter_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws) {
 // ---------------------------------------------------------------------------
 // 3. partition
 // ---------------------------------------------------------------------------
-// Segment of element (key[0..KW), idx) of bucket plan p: number of splitters
-// <= the element.  Keys past the bucket's K are zero on both sides.
-template <int KW>
+// Segment of the element (key[0..K), idx) of bucket plan p: the number of
+// splitters <= the element (splitters are sorted ascending).
+template <int K>
 __device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, const BucketPlan& p,
-                                                 const uint64_t (&key)[KW], uint32_t idx) {
+                                                 const uint64_t (&key)[K], uint32_t idx) {
   const uint32_t ns = p.g - 1;
   const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + p.spl_off);
-  const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(p.K) * ns);
+  const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(K) * ns);
   uint32_t lo = 0, hi = ns;  // answer in [0, ns]
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;  // is splitter mid-1 <= element ?
     const uint32_t s = mid - 1;
-    int c = 0;  // sign of (splitter - element)
+    bool le = false, decided = false;
 #pragma unroll
-    for (int k = 0; k < KW; ++k) {
-      if (c == 0 && k < static_cast<int>(p.K)) {
-        const uint64_t a = sk[k * ns + s];
-        c = a < key[k] ? -1 : (a > key[k] ? 1 : 0);
+    for (int k = 0; k < K; ++k) {
+      const uint64_t a = sk[k * ns + s];
+      if (!decided && a != key[k]) {
+        le = a < key[k];
+        decided = true;
       }
     }
-    const bool le = c < 0 || (c == 0 && si[s] <= idx);
+    if (!decided) le = si[s] <= idx;
     if (le) lo = mid;
     else hi = mid - 1;
   }
   return p.seg0 + lo;
+}
+
+// Record words raw[0..K) (as loaded) of word i, length L -> big-endian masked
+// keys in key[0..K) and the word's segment.
+template <int K, int KW>
+__device__ __forceinline__ uint32_t classify(uint64_t (&key)[KW], uint32_t i, uint32_t L,
+                                             const BucketPlan& p, const uint8_t* tab) {
+  uint64_t kk[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    kk[k] = bswap64(key[k]) & key_mask(L, k);
+    key[k] = kk[k];
+  }
+  return p.g > 1 ? find_segment<K>(tab, p, kk, i) : p.seg0;
 }
 
 template <int KW>
@@ -384,10 +402,11 @@ auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict
       const uint32_t i = base + u * 32 + lane;
       seg[u] = 0xFFFFFFFFu;
       if (L[u]) {
-#pragma unroll
-        for (int k = 0; k < KW; ++k) key[u][k] = bswap64(key[u][k]) & key_mask(L[u], k);
         const BucketPlan& p = plans[L[u]];
-        seg[u] = p.g > 1 ? find_segment<KW>(tab, p, key[u], i) : p.seg0;
+        if (KW == 1 || p.K == 1) seg[u] = classify<1, KW>(key[u], i, L[u], p, tab);
+        else if (KW == 2 || p.K == 2) seg[u] = classify<(KW >= 2 ? 2 : 1), KW>(key[u], i, L[u], p, tab);
+        else if (KW == 3 || p.K == 3) seg[u] = classify<(KW >= 3 ? 3 : 1), KW>(key[u], i, L[u], p, tab);
+        else seg[u] = classify<KW, KW>(key[u], i, L[u], p, tab);
       }
     }
     uint32_t peers[kPartWords], first[kPartWords];
@@ -396,20 +415,31 @@ auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict
       peers[u] = __match_any_sync(0xffffffffu, seg[u]);
       first[u] = 0;
       if (seg[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
-        first[u] = atomicAdd(&v.cursor[seg[u]], __popc(peers[u]));
+        first[u] = atomicAdd(&v.cursor[seg[u] * kCursorStride], __popc(peers[u]));
     }
 #pragma unroll
     for (uint32_t u = 0; u < kPartWords; ++u) {
       const uint32_t f = __shfl_sync(0xffffffffu, first[u], __ffs(peers[u]) - 1);
       if (seg[u] == 0xFFFFFFFFu) continue;
       const uint32_t pos = f + __popc(peers[u] & lanemask_lt());
-      const uint32_t rc = v.rcap[seg[u]];
+      const BucketPlan& p = plans[L[u]];
+      uint32_t rc;
+      uint64_t rb, ib;
+      if (!retry_pass) {
+        // optimistic layout: a pure function of the bucket plan
+        const uint32_t j = seg[u] - p.seg0;
+        rc = p.cap;
+        rb = p.r64 + static_cast<uint64_t>(j) * p.cap * p.K;
+        ib = p.r32 + static_cast<uint64_t>(j) * p.cap;
+      } else {
+        rc = v.rcap[seg[u]];
+        rb = v.rbase[seg[u]];
+        ib = v.ibase[seg[u]];
+      }
       if (pos < rc) {
-        const uint64_t rb = v.rbase[seg[u]], ib = v.ibase[seg[u]];
-        const uint32_t K = keys_for_len(L[u]);
 #pragma unroll
         for (int k = 0; k < KW; ++k)
-          if (k < static_cast<int>(K)) v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = key[u][k];
+          if (k < static_cast<int>(p.K)) v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = key[u][k];
         v.area32[ib + pos] = base + u * 32 + lane;
       } else {
         overflow = true;
@@ -440,7 +470,7 @@ auto_layout_kernel(uint32_t W, Ws ws) {
   // regions (index area) and region x K (key area)
   uint32_t c = 0, c4 = 0, ck = 0;
   for (uint32_t j = b; j < e; ++j) {
-    const uint32_t x = v.cursor[j];
+    const uint32_t x = v.cursor[j * kCursorStride];
     const uint32_t K = keys_for_len(v.segL[j]);
     c += x;
     c4 += exact_region(x, K);
@@ -452,7 +482,7 @@ auto_layout_kernel(uint32_t W, Ws ws) {
   uint32_t runk = block_exclusive_scan(ck, tmp, &totk);
   const bool fits = tot4 <= v.size32 && totk <= v.size64;
   for (uint32_t j = b; j < e; ++j) {
-    const uint32_t x = v.cursor[j];
+    const uint32_t x = v.cursor[j * kCursorStride];
     const uint32_t K = keys_for_len(v.segL[j]);
     v.outbase[j] = run;
     run += x;
@@ -463,7 +493,7 @@ auto_layout_kernel(uint32_t W, Ws ws) {
       v.rbase[j] = runk;
       run4 += r;
       runk += r * K;
-      v.cursor[j] = 0;
+      v.cursor[j * kCursorStride] = 0;
     }
   }
   if (threadIdx.x == 0 && redo) {
@@ -479,8 +509,8 @@ auto_layout_kernel(uint32_t W, Ws ws) {
 // strided accesses of the merge rounds free of bank conflicts.
 __device__ __forceinline__ uint32_t pad16(uint32_t i) { return i + (i >> 4); }
 
-// E elements per thread for key count K (E x threads covers the capacity).
-template <int K> struct SegE { static constexpr int value = K == 1 ? 8 : (K == 2 ? 4 : 2); };
+// Elements per thread of the one-key (key, index) merge sort.
+template <int K> struct SegE { static constexpr int value = 8; };
 
 __host__ __device__ constexpr size_t seg_plane_elems(uint32_t K) {
   // padded capacity: pad16(cap - 1) + 1 rounded up to an even count
@@ -489,10 +519,11 @@ __host__ __device__ constexpr size_t seg_plane_elems(uint32_t K) {
 
 constexpr size_t kSegPlanesBytes = 104576;  // >= max over K of seg_plane_elems(K) x (8K + 4)
 
-// Two segment buffers (sort one while the next one arrives), two barriers.
+// One segment buffer per CTA (two CTAs per SM overlap each other's copies,
+// sorts and stores): barrier + planes.
 constexpr size_t kSegBufBytes = 16 + kSegPlanesBytes;
 __host__ __device__ constexpr size_t segsort_smem_bytes() {
-  return 128 + 2 * kSegBufBytes;  // alignment slack, buffers
+  return 128 + kSegBufBytes;  // alignment slack, buffer
 }
 
 template <int K>
@@ -680,7 +711,7 @@ __device__ void prefetch_segment(uint8_t* buf, const AutoView& v, uint32_t seg, 
 }
 
 __device__ __forceinline__ uint32_t seg_count(const AutoView& v, uint32_t seg) {
-  return min(v.cursor[seg], v.rcap[seg]);
+  return min(v.cursor[seg * kCursorStride], v.rcap[seg]);
 }
 
 // Thread 0: start the copy of segment `seg` into `buf` when it will be sorted
@@ -699,6 +730,195 @@ __device__ bool maybe_prefetch(uint8_t* buf, const AutoView& v, uint32_t seg, ui
   return true;
 }
 
+// ---- one-word composite elements -----------------------------------------
+// A one-key segment whose keys (without their zero tail bytes) span at most
+// kb bits and whose indices fit ib bits, with kb + ib <= 64, sorts as single
+// uint64 values ((key >> shift) - kmin) << ib | idx: the integer order of the
+// composites is the (key, index) order.
+
+__device__ __forceinline__ void cswap64(uint64_t& a, uint64_t& b) {
+  const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+  a = lo;
+  b = hi;
+}
+
+template <int E>
+__device__ __forceinline__ void sort_regs64(uint64_t (&r)[E]) {
+#pragma unroll
+  for (int k = 2; k <= E; k <<= 1) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int j = i ^ (k - 1);
+      if (j > i && (i & (k >> 1)) == 0) cswap64(r[i], r[j]);
+    }
+#pragma unroll
+    for (int jj = k >> 2; jj > 0; jj >>= 1) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int j = i ^ jj;
+        if (j > i) cswap64(r[i], r[j]);
+      }
+    }
+  }
+}
+
+// Register bitonic sort of N = E * blockDim.x positions, blocked layout:
+// thread t holds positions t*E .. t*E+E-1 in r[].  All-ascending form: for
+// each block size k the first step pairs i with i ^ (k-1), the next ones pair
+// i with i ^ j (j = k/4 .. 1); the lower position keeps the smaller value.
+// A partner in the same thread is compared in registers, one in the same warp
+// through __shfl_xor_sync, one in another warp through shared memory.  Every
+// compare-exchange of a step is independent, so all threads and warps work in
+// every step.  Ops supplies the element order, the warp shuffle and the
+// shared-memory exchange slots (padded positions).
+
+// Plain uint64 composites; exchange slots in plane[].
+struct U64Ops {
+  using T = uint64_t;
+  uint64_t* plane;
+  __device__ static bool less(uint64_t a, uint64_t b) { return a < b; }
+  __device__ static uint64_t shfl(uint64_t x, uint32_t m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+  __device__ static uint64_t inf() { return ~0ull; }
+  __device__ void st(uint32_t i, uint64_t v) const { plane[pad16(i)] = v; }
+  __device__ uint64_t ld(uint32_t i) const { return plane[pad16(i)]; }
+};
+
+// (key words, index) elements; exchange slots in the tile's planes.
+template <int K>
+struct ElemOps {
+  using T = Elem<K>;
+  SmemTile<K> t;
+  __device__ static bool less(const Elem<K>& a, const Elem<K>& b) { return elem_less<K>(a, b); }
+  __device__ static Elem<K> shfl(const Elem<K>& x, uint32_t m) {
+    Elem<K> y;
+#pragma unroll
+    for (int k = 0; k < K; ++k) y.k[k] = __shfl_xor_sync(0xffffffffu, x.k[k], m);
+    y.idx = __shfl_xor_sync(0xffffffffu, x.idx, m);
+    return y;
+  }
+  __device__ static Elem<K> inf() { return elem_inf<K>(); }
+  __device__ void st(uint32_t i, const Elem<K>& v) const { t.put(pad16(i), v); }
+  __device__ Elem<K> ld(uint32_t i) const { return t.get(pad16(i)); }
+};
+
+template <typename Ops, int M, int E>
+__device__ __forceinline__ void reg_step(typename Ops::T (&r)[E]) {
+  if constexpr (M < E) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      constexpr int m = M;
+      const int q = j ^ m;
+      if (q > j && Ops::less(r[q], r[j])) {
+        const typename Ops::T x = r[j];
+        r[j] = r[q];
+        r[q] = x;
+      }
+    }
+  }
+}
+
+template <typename Ops, int E>
+__device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops& ops, uint32_t mask) {
+  using T = typename Ops::T;
+  constexpr uint32_t LE = E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane_mask = mask >> LE;
+  if (mask < E) {
+    // in registers: masks are the flips 1, 3, 7, 15 or the cleaners 1, 2, 4, 8
+    switch (mask) {
+      case 1: reg_step<Ops, 1, E>(r); break;
+      case 2: reg_step<Ops, 2, E>(r); break;
+      case 3: reg_step<Ops, 3, E>(r); break;
+      case 4: reg_step<Ops, 4, E>(r); break;
+      case 7: reg_step<Ops, 7, E>(r); break;
+      case 8: reg_step<Ops, 8, E>(r); break;
+      default: reg_step<Ops, 15, E>(r); break;
+    }
+  } else if (lane_mask < 32) {
+    // across lanes of one warp; my position is the upper one of its pair when
+    // the highest bit of the lane part of the mask is set in my lane
+    const uint32_t top = 1u << (31 - __clz(lane_mask));
+    const bool keep_small = (tid & top) == 0;
+    if ((mask & (E - 1)) == 0) {
+      // cleaner step: the partner holds the same slot j
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const T other = Ops::shfl(r[j], lane_mask);
+        if (Ops::less(other, r[j]) == keep_small) r[j] = other;
+      }
+    } else {
+      // flip step (mask = k - 1): slot j pairs with the partner's slot E-1-j.
+      // Slots j and E-1-j are exchanged together: sending slot E-1-j delivers
+      // the partner's value for my slot j, sending slot j the one for E-1-j.
+#pragma unroll
+      for (int j = 0; j < E / 2; ++j) {
+        const T for_j = Ops::shfl(r[E - 1 - j], lane_mask);
+        const T for_m = Ops::shfl(r[j], lane_mask);
+        if (Ops::less(for_j, r[j]) == keep_small) r[j] = for_j;
+        if (Ops::less(for_m, r[E - 1 - j]) == keep_small) r[E - 1 - j] = for_m;
+      }
+    }
+  } else {
+    // across warps: exchange through shared memory
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) ops.st(tid * E + j, r[j]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const uint32_t i = tid * E + j, pi = i ^ mask;
+      const T other = ops.ld(pi);
+      if (Ops::less(other, r[j]) == (i < pi)) r[j] = other;
+    }
+  }
+}
+
+// Sorts the first c values (read by get(i), unpadded) with a register bitonic
+// network of E per thread and hands them to sink(pos, value).  Needs
+// c <= E * blockDim.x; ops' exchange slots must hold pad16(E*blockDim.x - 1) + 1.
+template <typename Ops, int E, typename Get, typename Sink>
+__device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
+  using T = typename Ops::T;
+  const uint32_t tid = threadIdx.x;
+  T r[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const uint32_t i = tid * E + j;
+    r[j] = i < c ? get(i) : Ops::inf();
+  }
+  uint32_t N = 2;
+  while (N < c) N <<= 1;
+  if (N < E) N = E;
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    bitonic_step<Ops, E>(r, ops, k - 1);
+    for (uint32_t j = k >> 2; j > 0; j >>= 1) bitonic_step<Ops, E>(r, ops, j);
+  }
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (tid * E + j < c) sink(tid * E + j, r[j]);
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t warp_min64(uint64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y < x ? y : x;
+  }
+  return x;
+}
+__device__ __forceinline__ uint64_t warp_max64(uint64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+// Segments of words with two or more key words (longer than 8 letters, a
+// small share of typical text): bitonic network in shared memory, which keeps
+// no elements in registers.
 template <int K>
 __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c,
                               uint32_t W, uint8_t* out_rec, uint32_t* out_perm) {
@@ -708,75 +928,144 @@ __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uin
 #pragma unroll
   for (int k = 0; k < K; ++k) t.k[k] = kp + k * C;
   t.idx = reinterpret_cast<uint32_t*>(kp + static_cast<size_t>(K) * C);
-  block_merge_sort_out<K, SegE<K>::value>(t, c, W, v.outbase[seg], out_rec, out_perm);
+  bitonic_flip<K>(t, c);
+  __syncthreads();
+  const uint32_t ob = v.outbase[seg];
+  for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) write_word<K>(W, out_rec, out_perm, ob + r, t.get(r));
+  __syncthreads();
 }
 
-// Persistent CTAs walk the segments; while one segment is sorted in one
-// shared-memory buffer, the bulk copy of the CTA's next segment fills the
-// other buffer.
-__global__ void __launch_bounds__(kSegThreads, 1)
+// One-key segment of length-L words resident in buf: composite sort when the
+// key span and index width fit 64 bits, else the (key, index) merge sort.
+__device__ void sort_resident_k1(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c,
+                                 uint32_t L, uint32_t W, uint8_t* out_rec, uint32_t* out_perm) {
+  __shared__ uint64_t red[3][kSegThreads / 32];
+  __shared__ uint64_t s_kmin;
+  __shared__ uint32_t s_kb, s_ib;
+  uint64_t* kp = reinterpret_cast<uint64_t*>(buf + 16);
+  const uint32_t C = static_cast<uint32_t>(seg_plane_elems(1));
+  uint32_t* ip = reinterpret_cast<uint32_t*>(kp + C);
+  const uint32_t shift = 64 - 8 * L;  // L <= 8: the low 64-8L key bits are zero
+  uint64_t kmin = ~0ull, kmax = 0, imax = 0;
+  for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
+    const uint64_t k = kp[i] >> shift;
+    kmin = k < kmin ? k : kmin;
+    kmax = k > kmax ? k : kmax;
+    imax = ip[i] > imax ? ip[i] : imax;
+  }
+  kmin = warp_min64(kmin);
+  kmax = warp_max64(kmax);
+  imax = warp_max64(imax);
+  const uint32_t warp = threadIdx.x >> 5;
+  if (lane_id() == 0) {
+    red[0][warp] = kmin;
+    red[1][warp] = kmax;
+    red[2][warp] = imax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t a = ~0ull, b = 0, m = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+      a = red[0][w] < a ? red[0][w] : a;
+      b = red[1][w] > b ? red[1][w] : b;
+      m = red[2][w] > m ? red[2][w] : m;
+    }
+    s_kmin = a;
+    s_kb = b == a ? 0u : 64u - static_cast<uint32_t>(__clzll(b - a));
+    s_ib = 32u - static_cast<uint32_t>(__clz(static_cast<uint32_t>(m) | 1u));
+  }
+  __syncthreads();
+  const uint32_t kb = s_kb, ib = s_ib;
+  const uint64_t k0 = s_kmin;
+  const uint32_t ob = v.outbase[seg];
+  if (kb + ib <= 64) {
+    for (uint32_t i = threadIdx.x; i < c; i += blockDim.x)
+      kp[i] = (((kp[i] >> shift) - k0) << ib) | ip[i];
+    __syncthreads();
+    const uint64_t imask = (1ull << ib) - 1;
+    auto sink = [&](uint32_t pos, uint64_t x) {
+      Elem<1> e;
+      e.k[0] = ((x >> ib) + k0) << shift;
+      e.idx = static_cast<uint32_t>(x & imask);
+      write_word<1>(W, out_rec, out_perm, ob + pos, e);
+    };
+    const U64Ops ops{kp};
+    auto get = [&](uint32_t i) { return kp[i]; };
+    // reads happen before the first exchange writes (each step syncs first)
+    if (c <= 4 * blockDim.x) block_sort<U64Ops, 4>(ops, c, get, sink);
+    else if (c <= 8 * blockDim.x) block_sort<U64Ops, 8>(ops, c, get, sink);
+    else block_sort<U64Ops, 16>(ops, c, get, sink);
+  } else {
+    SmemTile<1> t;
+    t.k[0] = kp;
+    t.idx = ip;
+    const ElemOps<1> ops{t};
+    auto get = [&](uint32_t i) { return t.get(i); };
+    auto sink = [&](uint32_t pos, const Elem<1>& e) { write_word<1>(W, out_rec, out_perm, ob + pos, e); };
+    if (c <= 4 * blockDim.x) block_sort<ElemOps<1>, 4>(ops, c, get, sink);
+    else if (c <= 8 * blockDim.x) block_sort<ElemOps<1>, 8>(ops, c, get, sink);
+    else {
+      // rare: a wide-key segment above 4096 words
+      bitonic_flip<1>(t, c);
+      __syncthreads();
+      for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) write_word<1>(W, out_rec, out_perm, ob + r, t.get(r));
+      __syncthreads();
+    }
+  }
+}
+
+// Persistent CTAs (two per SM) walk the segments: bulk-copy the segment into
+// shared memory, sort, write the output records and permutation.
+__global__ void __launch_bounds__(kSegThreads, 2)
 auto_segsort_kernel(uint32_t W, Ws ws, uint8_t* __restrict__ out_rec,
                     uint32_t* __restrict__ out_perm) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ int s_issued[2];
-  uint8_t* smem = align128(smem_raw);
-  uint8_t* const buf0 = smem;
-  uint8_t* const buf1 = smem + kSegBufBytes;
+  uint8_t* buf = align128(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf);
   const AutoView v = auto_view(ws, W);
   const uint32_t G = v.hdr->G;
   if (threadIdx.x == 0) {
-    mbar_init(reinterpret_cast<uint64_t*>(buf0), 1);
-    mbar_init(reinterpret_cast<uint64_t*>(buf1), 1);
+    mbar_init(bar, 1);
     fence_barrier_init();
-    s_issued[0] = maybe_prefetch(buf0, v, blockIdx.x, G) ? 1 : 0;
-    s_issued[1] = 0;
   }
   __syncthreads();
-  uint32_t ph0 = 0, ph1 = 0;  // barrier phases of the two buffers
-  uint32_t it = 0;
-  bool failed = false;
-  for (uint32_t seg = blockIdx.x; seg < G; seg += gridDim.x, ++it) {
-    const bool odd = (it & 1u) != 0;
-    uint8_t* const cur = odd ? buf1 : buf0;
-    uint8_t* const nxt = odd ? buf0 : buf1;
-    // every thread is done with the other buffer (previous segment): hand it
-    // to the async proxy and start the next copy
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) s_issued[odd ? 0 : 1] = maybe_prefetch(nxt, v, seg + gridDim.x, G) ? 1 : 0;
+  uint32_t phase = 0;
+  for (uint32_t seg = blockIdx.x; seg < G; seg += gridDim.x) {
     const uint32_t c = seg_count(v, seg);
-    const uint32_t K = keys_for_len(v.segL[seg]);
+    const uint32_t L = v.segL[seg];
+    const uint32_t K = keys_for_len(L);
     if (c == 0) continue;
-    if (s_issued[odd ? 1 : 0]) {
-      const bool ok = mbar_wait_bounded(reinterpret_cast<uint64_t*>(cur), odd ? ph1 : ph0);
-      if (odd) ph1 ^= 1u;
-      else ph0 ^= 1u;
-      if (!__syncthreads_and(ok)) {
-        failed = true;
-        break;
-      }
-      switch (K) {
-        case 1: sort_resident<1>(cur, v, seg, c, W, out_rec, out_perm); break;
-        case 2: sort_resident<2>(cur, v, seg, c, W, out_rec, out_perm); break;
-        case 3: sort_resident<3>(cur, v, seg, c, W, out_rec, out_perm); break;
-        default: sort_resident<4>(cur, v, seg, c, W, out_rec, out_perm); break;
-      }
-    } else {
+    if (c > auto_seg_cap(K)) {
       // larger than shared memory (after a retry): chunked sort + merges
-      uint8_t* scratch = cur + 16;
+      uint8_t* scratch = buf + 16;
       switch (K) {
         case 1: segsort_big<1>(scratch, v, seg, c, W, out_rec, out_perm); break;
         case 2: segsort_big<2>(scratch, v, seg, c, W, out_rec, out_perm); break;
         case 3: segsort_big<3>(scratch, v, seg, c, W, out_rec, out_perm); break;
         default: segsort_big<4>(scratch, v, seg, c, W, out_rec, out_perm); break;
       }
+      continue;
     }
-  }
-  if (failed && threadIdx.x == 0) {
-    set_error(ws.hdr, BSORT_E_TIMEOUT);
-    // let copies in flight land before the CTA exits
-    if (s_issued[0]) mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf0), ph0);
-    if (s_issued[1]) mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf1), ph1);
+    // earlier generic-proxy use of the buffer must be ordered before the bulk
+    // copy (async proxy) overwrites it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) maybe_prefetch(buf, v, seg, G);
+    const bool ok = mbar_wait_bounded(bar, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        set_error(ws.hdr, BSORT_E_TIMEOUT);
+        mbar_wait_bounded(bar, phase ^ 1u);  // let the copy in flight land before exiting
+      }
+      return;
+    }
+    switch (K) {
+      case 1: sort_resident_k1(buf, v, seg, c, L, W, out_rec, out_perm); break;
+      case 2: sort_resident<2>(buf, v, seg, c, W, out_rec, out_perm); break;
+      case 3: sort_resident<3>(buf, v, seg, c, W, out_rec, out_perm); break;
+      default: sort_resident<4>(buf, v, seg, c, W, out_rec, out_perm); break;
+    }
   }
 }
 
@@ -863,10 +1152,8 @@ __global__ void auto_offsets_kernel(uint32_t W, Ws ws, uint32_t* __restrict__ of
 static_assert(seg_plane_elems(1) * 12 <= kSegPlanesBytes && seg_plane_elems(2) * 20 <= kSegPlanesBytes &&
                   seg_plane_elems(3) * 28 <= kSegPlanesBytes && seg_plane_elems(4) * 36 <= kSegPlanesBytes,
               "segment planes exceed the shared-memory budget");
-static_assert(SegE<1>::value * kSegThreads >= 8192 && SegE<2>::value * kSegThreads >= 4096 &&
-                  SegE<3>::value * kSegThreads >= 2048 && SegE<4>::value * kSegThreads >= 2048,
-              "E x threads must cover the segment capacity");
-static_assert(segsort_smem_bytes() <= 227 * 1024, "segsort buffers exceed shared memory");
+static_assert(16 * kSegThreads >= 8192, "composite E x threads must cover the segment capacity");
+static_assert(2 * (segsort_smem_bytes() + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");
 
 int g_sm_count = 0;
 

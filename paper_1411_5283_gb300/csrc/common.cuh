@@ -74,7 +74,9 @@ constexpr size_t auto_bytes(uint64_t cap, uint32_t W) {
     const uint32_t K = (L + 7) / 8;
     samples += static_cast<size_t>(auto_sample_cap(K, cap)) * (8 * K + 4);
   }
-  const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 4 * 5 + 8 * 2);
+  // splitters (8 KW + 4), cursors (one 128-byte line each), four u32 and two
+  // u64 tables per segment
+  const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 128 + 4 * 4 + 8 * 2);
   return align_up(4096 + samples + tables + 4096, 256);
 }
 
