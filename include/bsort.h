@@ -188,6 +188,30 @@ bsort_status bsort_sort_records_noalloc(const uint8_t* d_rec, const uint8_t* d_l
                                         uint8_t* d_out_rec, uint32_t* d_out_perm,
                                         uint32_t* d_off, int32_t* d_status, cudaStream_t s);
 
+/* Batched form (not in the paper; its §4 MPI chunking sorts one text): sorts
+ * n_lists independent lists with one stream of persistent kernels that can be
+ * captured in one CUDA graph (phases 1-3 of §3 for every list at once).
+ * d_lists[n_lists] (device) describes each list.  Record mode
+ * (lists_are_text = 0): d_text_or_rec / d_len hold all lists' records.  Text
+ * mode: d_text_or_rec holds the texts, d_len must be NULL, and the tokenised
+ * words go to the output slots only.  For list i the outputs are
+ * d_out_rec[(word_off + r) * W], d_out_perm[word_off + r] (index within the
+ * list), d_out_off[i * (W + 2) + L], and d_list_status[i] (a bsort_status).
+ * max_list_words bounds every list's word count (it sets the number of merge
+ * passes); a longer list gets BSORT_E_CAPACITY.  Every list's slots
+ * word_off .. word_off + max_words - 1 must lie below the word capacity the
+ * workspace was sized for (bsort_sort_many_workspace_size(total_words,
+ * n_lists, W); a list outside it gets BSORT_E_WORKSPACE).  alg BSORT_AUTO
+ * means BSORT_MERGE here.  Per-list statuses are written to d_list_status;
+ * the call itself returns only argument and launch errors. */
+size_t bsort_sort_many_workspace_size(uint64_t total_words, uint32_t n_lists, uint32_t W);
+bsort_status bsort_sort_many(const uint8_t* d_text_or_rec, const uint8_t* d_len,
+                             const bsort_list* d_lists, uint32_t n_lists, uint32_t W,
+                             int lists_are_text, uint32_t max_list_words, bsort_alg alg,
+                             const bsort_tune* tune, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                             uint32_t* d_out_off, int32_t* d_list_status, void* d_ws,
+                             size_t ws_bytes, cudaStream_t s);
+
 /* Copies the bucket contents left in the workspace by bsort_bucket_by_length
  * or bsort_sort_buckets (for inspection and tests): d_keys[k*n + r] is key
  * word k of bucket position r (0 beyond the word's ceil(L/8) keys),

@@ -62,6 +62,12 @@ _SIGS = {
     "bsort_sort_records_noalloc": (ctypes.c_int, [c_u8p, c_u8p, ctypes.c_uint32, ctypes.c_uint32,
                                                   ctypes.c_int, ctypes.POINTER(Tune), c_u8p,
                                                   c_u8p, c_u8p, c_u8p, c_u8p]),
+    "bsort_sort_many_workspace_size": (c_size, [ctypes.c_uint64, ctypes.c_uint32,
+                                                ctypes.c_uint32]),
+    "bsort_sort_many": (ctypes.c_int, [c_u8p, c_u8p, c_u8p, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                                       ctypes.POINTER(Tune), c_u8p, c_u8p, c_u8p, c_u8p, c_u8p,
+                                       c_size, c_u8p]),
     "bsort_export_buckets": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, c_u8p, c_u8p,
                                             c_size, c_u8p, c_u8p, c_u8p]),
     "bsort_profile_enable": (ctypes.c_int, [ctypes.c_int]),

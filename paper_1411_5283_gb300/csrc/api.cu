@@ -195,6 +195,35 @@ bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W
   return cuda_status(e);
 }
 
+size_t bsort_sort_many_workspace_size(uint64_t total_words, uint32_t n_lists, uint32_t W) {
+  if (!valid_W(W) || total_words > 0xFFFFFFF0ull) return 0;
+  return many_workspace_size(total_words, n_lists, W);
+}
+
+bsort_status bsort_sort_many(const uint8_t* d_text_or_rec, const uint8_t* d_len,
+                             const bsort_list* d_lists, uint32_t n_lists, uint32_t W,
+                             int lists_are_text, uint32_t max_list_words, bsort_alg alg,
+                             const bsort_tune* tune, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                             uint32_t* d_out_off, int32_t* d_list_status, void* d_ws,
+                             size_t ws_bytes, cudaStream_t s) {
+  if (!valid_W(W)) return BSORT_E_INVALID;
+  if (n_lists == 0) return BSORT_OK;
+  if (!d_lists || !d_out_off || !d_list_status || !d_out_rec || !d_out_perm || !d_text_or_rec)
+    return BSORT_E_INVALID;
+  if (lists_are_text ? d_len != nullptr : d_len == nullptr) return BSORT_E_INVALID;
+  if (!aligned(d_out_rec, 16) || (!lists_are_text && !aligned(d_text_or_rec, 16)))
+    return BSORT_E_INVALID;
+  if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
+  if (max_list_words == 0) return BSORT_E_INVALID;
+  SortParams p;
+  if (!resolve(alg, tune, W, &p)) return BSORT_E_INVALID;
+  if (!d_ws || !aligned(d_ws, 256) || many_capacity(ws_bytes, W, n_lists) == 0)
+    return BSORT_E_WORKSPACE;
+  return cuda_status(launch_many(d_text_or_rec, d_len, d_lists, n_lists, W, lists_are_text != 0,
+                                 max_list_words, p, d_out_off, d_out_rec, d_out_perm,
+                                 d_list_status, d_ws, ws_bytes, s));
+}
+
 bsort_status bsort_export_buckets(uint32_t n, uint32_t W, const uint32_t* d_off,
                                   const void* d_ws, size_t ws_bytes, uint64_t* d_keys,
                                   uint32_t* d_idx, cudaStream_t s) {

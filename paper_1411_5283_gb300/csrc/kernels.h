@@ -68,6 +68,15 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
 cudaError_t launch_gather(uint32_t n_cap, const uint32_t* d_n, uint32_t W, const uint32_t* d_off,
                           const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
 
+// Batched sort (sort_many.cu).
+size_t many_workspace_size(uint64_t total_words, uint32_t n_lists, uint32_t W);
+uint64_t many_capacity(size_t ws_bytes, uint32_t W, uint32_t n_lists);
+cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bsort_list* lists,
+                        uint32_t n_lists, uint32_t W, int text, uint32_t max_list_words,
+                        const SortParams& p, uint32_t* out_off, uint8_t* out_rec,
+                        uint32_t* out_perm, int32_t* list_status, void* d_ws, size_t ws_bytes,
+                        cudaStream_t s);
+
 cudaError_t launch_export(uint32_t n, uint32_t W, const uint32_t* d_off, const Ws& ws,
                           uint64_t* keys, uint32_t* idx, cudaStream_t s);
 

@@ -136,6 +136,10 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
   const uint32_t ks = tr.start & ~1u, is = tr.start & ~3u;
   const uint32_t kbytes = ((tr.start + tr.len - ks) * 8 + 15) & ~15u;
   const uint32_t ibytes = ((tr.start + tr.len - is) * 4 + 15) & ~15u;
+  // a persistent caller reuses this shared memory: order its earlier generic
+  // accesses before the bulk copy (async proxy) and start a fresh barrier
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -156,6 +160,8 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
     }
     return;
   }
+  // every thread has passed the wait: retire the barrier
+  if (threadIdx.x == 0) mbar_inval(bar);
   SmemTile<K> t;
 #pragma unroll
   for (int j = 0; j < K; ++j) t.k[j] = kplane + j * (T + 2) + (tr.start - ks);

@@ -15,39 +15,11 @@
 #include "block_scan.cuh"
 #include "common.cuh"
 #include "kernels.h"
+#include "tok_impl.cuh"
 
 namespace bsort {
 
 namespace {
-
-constexpr uint32_t kTokThreads = 256;
-constexpr uint32_t kTokWarps = kTokThreads / 32;
-constexpr uint32_t kSteps = 16;                       // 32-byte steps per warp per chunk
-constexpr uint32_t kWarpBytes = 32 * kSteps;          // 512
-constexpr uint32_t kChunkBytes = kTokWarps * kWarpBytes;  // 4096 per block iteration
-
-__device__ __forceinline__ bool letter_at(const uint8_t* __restrict__ text, uint32_t end,
-                                          uint32_t q) {
-  return q < end && is_letter(__ldg(text + q));
-}
-
-// Word-start masks of the warp's kSteps x 32 bytes starting at p (bytes at or
-// past `end` are separators); returns the number of starts.
-__device__ __forceinline__ uint32_t warp_starts(const uint8_t* __restrict__ text, uint32_t n,
-                                                uint32_t end, uint32_t p,
-                                                uint32_t (&starts)[kSteps]) {
-  const uint32_t lane = lane_id();
-  uint32_t carry = (p > 0 && p - 1 < n && is_letter(__ldg(text + p - 1))) ? 1u : 0u;
-  uint32_t cnt = 0;
-#pragma unroll
-  for (uint32_t st = 0; st < kSteps; ++st) {
-    const uint32_t letters = __ballot_sync(0xffffffffu, letter_at(text, end, p + 32 * st + lane));
-    starts[st] = letters & ~((letters << 1) | carry);
-    carry = letters >> 31;
-    cnt += __popc(starts[st]);
-  }
-  return cnt;
-}
 
 __global__ void __launch_bounds__(kTokThreads)
 tok_count_kernel(const uint8_t* __restrict__ text, uint32_t n, uint32_t per,
@@ -59,7 +31,7 @@ tok_count_kernel(const uint8_t* __restrict__ text, uint32_t n, uint32_t per,
   uint32_t cnt = 0;
   for (uint32_t c = b0; c < b1; c += kChunkBytes) {
     uint32_t starts[kSteps];
-    cnt += warp_starts(text, n, b1, c + warp * kWarpBytes, starts);
+    cnt += warp_starts(text, 0u, n, b1, c + warp * kWarpBytes, starts);
   }
   uint32_t total;
   block_exclusive_scan(lane_id() == 0 ? cnt : 0u, tmp, &total);
@@ -80,7 +52,7 @@ tok_write_kernel(const uint8_t* __restrict__ text, uint32_t n, uint32_t per, uin
   for (uint32_t c = b0; c < b1; c += kChunkBytes) {
     const uint32_t p = c + warp * kWarpBytes;
     uint32_t starts[kSteps];
-    const uint32_t cnt = warp_starts(text, n, b1, p, starts);
+    const uint32_t cnt = warp_starts(text, 0u, n, b1, p, starts);
     uint32_t total;
     uint32_t id = base + block_exclusive_scan(lane == 0 ? cnt : 0u, tmp, &total);
     id = __shfl_sync(0xffffffffu, id, 0);

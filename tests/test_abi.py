@@ -30,7 +30,7 @@ def declared() -> list[str]:
 def test_header_declares_the_abi():
     names = declared()
     for want in ["bsort_tokenize", "bsort_bucket_by_length", "bsort_sort_buckets",
-                 "bsort_gather", "bsort_workspace_size",
+                 "bsort_gather", "bsort_sort_many", "bsort_workspace_size",
                  "bsort_get_status", "bsort_status_string"]:
         assert want in names
 
@@ -65,3 +65,21 @@ def test_workspace_size_roundtrip(lib):
 def test_status_strings(lib):
     for c in range(8):
         assert lib.status_string(c) and "unknown" not in lib.status_string(c)
+
+
+def test_list_descriptor_layout():
+    import ctypes
+    from paper_1411_5283_gb300 import _lib as L, batch
+    assert batch.LIST_DTYPE.itemsize == ctypes.sizeof(L.ListDesc) == 32
+    d = batch.record_lists([3, 0, 5], capacity=[4, 1, 5])
+    assert d["word_off"].tolist() == [0, 4, 5]
+    assert d["n_words"].tolist() == [3, 0, 5] and d["max_words"].tolist() == [4, 1, 5]
+    t = batch.text_lists([10, 0, 7], [6, 1, 4])
+    assert t["text_off"].tolist() == [0, 10, 10] and t["word_off"].tolist() == [0, 6, 7]
+
+
+def test_sort_many_workspace_size(lib):
+    L = lib.load()
+    b = L.bsort_sort_many_workspace_size(1000, 10, 16)
+    assert b > 0 and L.bsort_sort_many_workspace_size(1000, 10, 12) == 0
+    assert L.bsort_sort_many_workspace_size(2000, 10, 16) > b
