@@ -39,7 +39,7 @@ namespace bsort {
 namespace {
 
 constexpr uint32_t kPartThreads = 512;
-constexpr uint32_t kSplSmem = 100 * 1024;          // splitter table staged up to this size
+constexpr uint32_t kSplSmem = 110 * 1024;          // splitter table staged up to this size
 constexpr uint32_t kSegThreads = 512;
 // One cursor per 128-byte line: the partition's atomics then spread over all
 // L2 slices instead of piling onto the few lines a packed array would use.
@@ -96,7 +96,7 @@ __host__ __device__ AutoView auto_view(const Ws& ws, uint32_t W) {
   o += align_up(4 * s32, 16);
   const uint64_t G = auto_max_segments(cap);
   v.spl = p + o;
-  o += align_up(G * (8 * KW + 4) + 16 * kBins, 16);
+  o += align_up(G * (8 * KW + 4) + (16 + kAutoDirBytes) * kBins, 16);
   v.rbase = reinterpret_cast<uint64_t*>(p + o);
   o += 8 * G;
   v.ibase = reinterpret_cast<uint64_t*>(p + o);
@@ -144,8 +144,13 @@ __device__ void bucket_geometry(uint32_t cnt, uint32_t K, uint32_t* g, uint32_t*
   }
 }
 
+// A bucket's splitter block: a 257-entry directory on the first key byte
+// (dir[b] = splitters whose first byte is below b), then K key planes and the
+// index plane of its g - 1 splitters.
+constexpr uint32_t kDirBytes = kAutoDirBytes;
+
 __device__ __forceinline__ uint32_t spl_bytes_of(uint32_t g, uint32_t K) {
-  return g >= 2 ? static_cast<uint32_t>(align_up((g - 1) * (8 * K + 4), 16)) : 0u;
+  return g >= 2 ? static_cast<uint32_t>(kDirBytes + align_up((g - 1) * (8 * K + 4), 16)) : 0u;
 }
 
 __device__ BucketPlan plan_for(const uint32_t* off, uint32_t L, uint64_t cap_ws) {
@@ -256,19 +261,35 @@ __device__ void choose_splitters(uint8_t* smem, const AutoView& v, const BucketP
   // floor((s+1) m / g); with no samples every splitter is +inf, so all words
   // land in the first segment (overflow then gives it an exact region)
   const uint32_t ns = p.g - 1;
-  uint64_t* sk = reinterpret_cast<uint64_t*>(v.spl + p.spl_off);
+  uint16_t* dir = reinterpret_cast<uint16_t*>(v.spl + p.spl_off);
+  uint64_t* sk = reinterpret_cast<uint64_t*>(v.spl + p.spl_off + kDirBytes);
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + static_cast<size_t>(K) * ns);
+  auto rank_of = [&](uint32_t s) {
+    return static_cast<uint32_t>((static_cast<uint64_t>(s + 1) * m) / p.g);
+  };
   for (uint32_t s = threadIdx.x; s < ns; s += blockDim.x) {
     if (m == 0) {
 #pragma unroll
       for (int k = 0; k < K; ++k) sk[k * ns + s] = ~0ull;
       si[s] = ~0u;
     } else {
-      const Elem<K> e = t.get(static_cast<uint32_t>((static_cast<uint64_t>(s + 1) * m) / p.g));
+      const Elem<K> e = t.get(rank_of(s));
 #pragma unroll
       for (int k = 0; k < K; ++k) sk[k * ns + s] = e.k[k];
       si[s] = e.idx;
     }
+  }
+  // directory: dir[b] = number of splitters whose first byte is below b
+  // (splitters are sorted, so their first bytes never decrease)
+  for (uint32_t b = threadIdx.x; b <= 256; b += blockDim.x) {
+    uint32_t lo = 0, hi = ns;  // first splitter with first byte >= b
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint64_t k0 = m == 0 ? ~0ull : t.k[0][rank_of(mid)];
+      if ((k0 >> 56) < b) lo = mid + 1;
+      else hi = mid;
+    }
+    dir[b] = static_cast<uint16_t>(lo);
   }
 }
 
@@ -320,9 +341,13 @@ template <int K>
 __device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, const BucketPlan& p,
                                                  const uint64_t (&key)[K], uint32_t idx) {
   const uint32_t ns = p.g - 1;
-  const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + p.spl_off);
+  const uint16_t* dir = reinterpret_cast<const uint16_t*>(tab + p.spl_off);
+  const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + p.spl_off + kDirBytes);
   const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(K) * ns);
-  uint32_t lo = 0, hi = ns;  // answer in [0, ns]
+  // splitters below dir[c] have a smaller first byte (all <= the element),
+  // those from dir[c+1] on a larger one; search only between
+  const uint32_t c = static_cast<uint32_t>(key[0] >> 56);
+  uint32_t lo = dir[c], hi = dir[c + 1];  // answer in [lo, hi]
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;  // is splitter mid-1 <= element ?
     const uint32_t s = mid - 1;
@@ -899,6 +924,78 @@ __device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
   __syncthreads();
 }
 
+// LSD radix sort of c uint64 values on their low `bits` bits, 8 bits per
+// pass, stable: each pass counts digits per warp over warp-contiguous ranges
+// (warp w owns positions [w S, (w+1) S)), scans the (digit, warp) counts in
+// digit-major order, then every warp writes its values in position order to
+// base[digit][warp] + (earlier equal digits in the warp).  A and B hold c
+// values each (A the input), hist 16 x 256 counters (one row per warp of a
+// 512-thread block).  Returns the array holding the result.
+constexpr uint32_t kRadixWarps = kSegThreads / 32;
+constexpr uint32_t kRadixMaxC = 5504;  // A, B and hist fit one segment buffer
+
+__device__ uint64_t* block_radix_u64(uint64_t* A, uint64_t* B, uint32_t* hist, uint32_t c,
+                                     uint32_t bits) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t S = ((c + kRadixWarps - 1) / kRadixWarps + 31) / 32 * 32;
+  const uint32_t w0 = min(c, warp * S), w1 = min(c, w0 + S);
+  uint32_t* row = hist + warp * 256;
+  uint64_t* src = A;
+  uint64_t* dst = B;
+  for (uint32_t shift = 0; shift < bits; shift += 8) {
+    for (uint32_t i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    // 1. counts per (warp, digit)
+    for (uint32_t b = w0; b < w1; b += 32) {
+      const uint32_t pos = b + lane;
+      const bool valid = pos < w1;
+      const uint32_t d = valid ? static_cast<uint32_t>(src[pos] >> shift) & 255u : 256u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid && lane == __ffs(peers) - 1) row[d] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // 2. exclusive scan in digit-major, warp-minor order (entry d * 16 + w)
+    {
+      __shared__ uint32_t tmp[kSegThreads / 32 + 1];
+      constexpr uint32_t per = kRadixWarps * 256 / kSegThreads;  // 8 entries per thread
+      uint32_t v[per], sum = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) {
+        const uint32_t e = threadIdx.x * per + k, d = e / kRadixWarps, w = e % kRadixWarps;
+        v[k] = hist[w * 256 + d];
+        sum += v[k];
+      }
+      uint32_t tot;
+      uint32_t run = block_exclusive_scan(sum, tmp, &tot);
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) {
+        const uint32_t e = threadIdx.x * per + k, d = e / kRadixWarps, w = e % kRadixWarps;
+        hist[w * 256 + d] = run;
+        run += v[k];
+      }
+    }
+    __syncthreads();
+    // 3. stable scatter
+    for (uint32_t b = w0; b < w1; b += 32) {
+      const uint32_t pos = b + lane;
+      const bool valid = pos < w1;
+      const uint64_t x = valid ? src[pos] : 0ull;
+      const uint32_t d = valid ? static_cast<uint32_t>(x >> shift) & 255u : 256u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid) dst[row[d] + __popc(peers & lanemask_lt())] = x;
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) row[d] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint64_t* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
 __device__ __forceinline__ uint64_t warp_min64(uint64_t x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -989,6 +1086,16 @@ __device__ void sort_resident_k1(uint8_t* buf, const AutoView& v, uint32_t seg, 
       e.idx = static_cast<uint32_t>(x & imask);
       write_word<1>(W, out_rec, out_perm, ob + pos, e);
     };
+    if (c <= kRadixMaxC) {
+      // A = composites over the key plane; B and the counters reuse the (now
+      // dead) rest of the buffer
+      uint64_t* B = kp + kRadixMaxC;
+      uint32_t* hist = reinterpret_cast<uint32_t*>(kp + 2 * kRadixMaxC);
+      const uint64_t* res = block_radix_u64(kp, B, hist, c, kb + ib);
+      for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) sink(r, res[r]);
+      __syncthreads();
+      return;
+    }
     const U64Ops ops{kp};
     auto get = [&](uint32_t i) { return kp[i]; };
     // reads happen before the first exchange writes (each step syncs first)
@@ -1153,6 +1260,10 @@ static_assert(seg_plane_elems(1) * 12 <= kSegPlanesBytes && seg_plane_elems(2) *
                   seg_plane_elems(3) * 28 <= kSegPlanesBytes && seg_plane_elems(4) * 36 <= kSegPlanesBytes,
               "segment planes exceed the shared-memory budget");
 static_assert(16 * kSegThreads >= 8192, "composite E x threads must cover the segment capacity");
+static_assert((2 * kRadixMaxC * 8 + kRadixWarps * 256 * 4) <= kSegPlanesBytes,
+              "radix buffers exceed the segment buffer");
+static_assert(kRadixMaxC * 8 <= seg_plane_elems(1) * 8,
+              "the composite input must lie inside the key plane");
 static_assert(2 * (segsort_smem_bytes() + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");
 
 int g_sm_count = 0;

@@ -58,6 +58,7 @@ __host__ __device__ constexpr uint32_t auto_sample_max(uint32_t K) {
 constexpr uint32_t kAutoSampleEvery = 32;      // one stratified sample position per 32 words
 constexpr uint32_t kAutoMinWords = 65536;      // smaller inputs take the merge path
 constexpr uint64_t kAutoSlack = 1u << 18;      // extra elements of the third region
+constexpr uint32_t kAutoDirBytes = 528;        // first-byte directory per bucket (257 x u16)
 
 __host__ __device__ constexpr uint32_t auto_sample_cap(uint32_t K, uint64_t cap) {
   return static_cast<uint32_t>(
@@ -77,7 +78,7 @@ constexpr size_t auto_bytes(uint64_t cap, uint32_t W) {
   // splitters (8 KW + 4), cursors (one 128-byte line each), four u32 and two
   // u64 tables per segment
   const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 128 + 4 * 4 + 8 * 2);
-  return align_up(4096 + samples + tables + 4096, 256);
+  return align_up(4096 + samples + tables + (16 + kAutoDirBytes) * kBins + 4096, 256);
 }
 
 // Layout for a plane capacity of `cap` elements (a multiple of 64).
