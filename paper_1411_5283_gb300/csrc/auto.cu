@@ -10,11 +10,14 @@
 //                          with probability 1/4, 1/2, 1 for 1, 2, >= 3 key
 //                          words: about 20 samples per expected segment),
 //                          grouped by length bucket (phase 2's sub-arrays)
-//   auto_splitter_kernel   one CTA per bucket sorts its samples and picks
-//                          g_L - 1 splitters by (keys, index), so a word
-//                          repeated many times is split evenly by index;
+//   auto_spl_sort_kernel   eight CTAs per bucket sort chunks of its samples;
 //                          every segment gets a region of the shared-memory
 //                          capacity, three times its expected count
+//   auto_spl_select_kernel each sample's rank across the sorted chunks (binary
+//                          search) picks the g_L - 1 splitters by (keys,
+//                          index), so a word repeated many times is split
+//                          evenly by index
+//   auto_spl_dir_kernel    per bucket, the splitters' first-byte directory
 //   auto_partition_kernel  every word finds its segment by binary search over
 //                          the splitters (staged in shared memory) and takes a
 //                          slot with a warp-aggregated atomic; a slot past the
@@ -23,12 +26,13 @@
 //                          counts); on overflow, exact regions for a retry
 //   auto_partition_kernel  (again) the retry pass, a no-op unless overflow
 //   auto_segsort_kernel    one CTA per segment: bulk-copy (TMA) the segment
-//                          into shared memory, merge sort it (register sort of
-//                          E elements per thread, then merge-path rounds in
-//                          padded shared memory), write the final records and
-//                          permutation at the segment's output base; a segment
-//                          larger than shared memory (only after a retry) is
-//                          sorted in chunks and merged in global memory
+//                          into shared memory, sort it (one key word: LSD
+//                          radix sort of (key - kmin, index) items held in
+//                          registers; longer keys: bitonic network in shared
+//                          memory), write the final records and permutation at
+//                          the segment's output base; a segment larger than
+//                          shared memory (only after a retry) is sorted in
+//                          chunks and merged in global memory
 #include "block_scan.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -46,7 +50,6 @@ constexpr uint32_t kSegThreads = 512;
 constexpr uint32_t kCursorStride = 32;
 
 // words per lane kept in flight by the partition pass (fewer for wide keys)
-template <int KW> struct PartWords { static constexpr uint32_t value = KW <= 2 ? 4 : 2; };
 
 // ---------------------------------------------------------------------------
 // Device view of the AUTO area
@@ -202,10 +205,10 @@ __device__ void load_plans(BucketPlan* plans, uint32_t* s_off, const uint32_t* d
 __global__ void __launch_bounds__(256)
 auto_sample_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
                    uint32_t n_cap, const uint32_t* __restrict__ d_n, uint32_t W,
-                   const uint32_t* __restrict__ d_off, Ws ws) {
+                   const uint32_t* __restrict__ d_off, Ws ws, AutoView av) {
   __shared__ BucketPlan plans[kMaxW + 1];
   __shared__ uint32_t s_off[kMaxW + 2];
-  const AutoView v = auto_view(ws, W);
+  const AutoView& v = av;
   load_plans(plans, s_off, d_off, W, v.cap);
   const uint32_t n = word_count(n_cap, d_n);
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,74 +240,62 @@ auto_sample_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// 2. splitters and region layout (one CTA per bucket)
+// 2. splitters and region layout
 // ---------------------------------------------------------------------------
+// A bucket's m samples are cut into kSplChunks chunks, each sorted by its own
+// CTA; a sample's rank among all m is its position in its chunk plus, for
+// every other chunk, the number of that chunk's samples below it (samples are
+// distinct: the index is part of the element).  Splitter s (0 <= s < g-1) is
+// the sample of rank floor((s+1) m / g), the lower bound of segment s+1; with
+// no samples every splitter is +inf, so all words land in the first segment
+// (overflow then gives it an exact region).
+constexpr uint32_t kSplChunks = 8;
+__host__ __device__ constexpr uint32_t spl_chunk(uint32_t K) { return auto_sample_max(K) / kSplChunks; }
+constexpr size_t kSplSortSmem = static_cast<size_t>(spl_chunk(1)) * 12;  // max over K of chunk x (8K + 4)
+
 template <int K>
-__device__ void choose_splitters(uint8_t* smem, const AutoView& v, const BucketPlan& p, uint32_t L) {
-  const uint32_t m = min(v.hdr->samp_cnt[L], p.scap);
+__device__ SmemTile<K> sample_tile(const AutoView& v, const BucketPlan& p) {
+  SmemTile<K> t;
+#pragma unroll
+  for (int k = 0; k < K; ++k) t.k[k] = v.samp64 + p.s64 + static_cast<size_t>(k) * p.scap;
+  t.idx = v.samp32 + p.s32;
+  return t;
+}
+
+template <int K>
+__device__ void sort_sample_chunk(uint8_t* smem, const AutoView& v, const BucketPlan& p, uint32_t m,
+                                  uint32_t j) {
+  constexpr uint32_t CH = spl_chunk(K);
+  const uint32_t lo = j * CH;
+  if (lo >= m) return;
+  const uint32_t cnt = min(CH, m - lo);
+  const SmemTile<K> g = sample_tile<K>(v, p);
   SmemTile<K> t;
   uint64_t* kp = reinterpret_cast<uint64_t*>(smem);
 #pragma unroll
-  for (int j = 0; j < K; ++j) t.k[j] = kp + j * p.scap;
-  t.idx = reinterpret_cast<uint32_t*>(kp + K * p.scap);
-  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-    Elem<K> e;
-#pragma unroll
-    for (int j = 0; j < K; ++j) e.k[j] = v.samp64[p.s64 + j * p.scap + i];
-    e.idx = v.samp32[p.s32 + i];
-    t.put(i, e);
-  }
+  for (int k = 0; k < K; ++k) t.k[k] = kp + k * CH;
+  t.idx = reinterpret_cast<uint32_t*>(kp + K * CH);
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) t.put(i, g.get(lo + i));
   __syncthreads();
-  bitonic_flip<K>(t, m);
+  bitonic_flip<K>(t, cnt);
   __syncthreads();
-  // splitter s (0 <= s < g-1) = lower bound of segment s+1 = sample of rank
-  // floor((s+1) m / g); with no samples every splitter is +inf, so all words
-  // land in the first segment (overflow then gives it an exact region)
-  const uint32_t ns = p.g - 1;
-  uint16_t* dir = reinterpret_cast<uint16_t*>(v.spl + p.spl_off);
-  uint64_t* sk = reinterpret_cast<uint64_t*>(v.spl + p.spl_off + kDirBytes);
-  uint32_t* si = reinterpret_cast<uint32_t*>(sk + static_cast<size_t>(K) * ns);
-  auto rank_of = [&](uint32_t s) {
-    return static_cast<uint32_t>((static_cast<uint64_t>(s + 1) * m) / p.g);
-  };
-  for (uint32_t s = threadIdx.x; s < ns; s += blockDim.x) {
-    if (m == 0) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) sk[k * ns + s] = ~0ull;
-      si[s] = ~0u;
-    } else {
-      const Elem<K> e = t.get(rank_of(s));
-#pragma unroll
-      for (int k = 0; k < K; ++k) sk[k * ns + s] = e.k[k];
-      si[s] = e.idx;
-    }
-  }
-  // directory: dir[b] = number of splitters whose first byte is below b
-  // (splitters are sorted, so their first bytes never decrease)
-  for (uint32_t b = threadIdx.x; b <= 256; b += blockDim.x) {
-    uint32_t lo = 0, hi = ns;  // first splitter with first byte >= b
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      const uint64_t k0 = m == 0 ? ~0ull : t.k[0][rank_of(mid)];
-      if ((k0 >> 56) < b) lo = mid + 1;
-      else hi = mid;
-    }
-    dir[b] = static_cast<uint16_t>(lo);
-  }
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) g.put(lo + i, t.get(i));
 }
 
+// (a) grid (W, kSplChunks): CTA (L-1, j) sorts chunk j of bucket L's samples;
+// CTA (L-1, 0) also lays out the bucket's segment regions.
 __global__ void __launch_bounds__(1024)
-auto_splitter_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws) {
+auto_spl_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ BucketPlan p;
-  const AutoView v = auto_view(ws, W);
-  const uint32_t L = blockIdx.x + 1;
+  const AutoView& v = av;
+  const uint32_t L = blockIdx.x + 1, j = blockIdx.y;
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
   if (threadIdx.x == 0) {
     p = plan_for(s_off, L, v.cap);
-    if (L == W) {
+    if (L == W && j == 0) {
       const BucketPlan last = p;
       v.hdr->G = last.seg0 + last.g;
       v.hdr->spl_bytes = last.spl_off + spl_bytes_of(last.g, last.K);
@@ -315,83 +306,212 @@ auto_splitter_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws) {
     }
   }
   __syncthreads();
-  for (uint32_t j = threadIdx.x; j < p.g; j += blockDim.x) {
-    const uint32_t seg = p.seg0 + j;
-    v.cursor[seg * kCursorStride] = 0;
-    v.rcap[seg] = p.cap;
-    v.segL[seg] = L;
-    v.rbase[seg] = p.r64 + static_cast<uint64_t>(j) * p.cap * p.K;
-    v.ibase[seg] = p.r32 + static_cast<uint64_t>(j) * p.cap;
+  if (j == 0) {
+    for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) {
+      const uint32_t seg = p.seg0 + q;
+      v.cursor[seg * kCursorStride] = 0;
+      v.rcap[seg] = p.cap;
+      v.segL[seg] = L;
+      v.rbase[seg] = p.r64 + static_cast<uint64_t>(q) * p.cap * p.K;
+      v.ibase[seg] = p.r32 + static_cast<uint64_t>(q) * p.cap;
+    }
   }
   if (p.g < 2) return;
+  const uint32_t m = min(v.hdr->samp_cnt[L], p.scap);
   switch (p.K) {
-    case 1: choose_splitters<1>(smem, v, p, L); break;
-    case 2: choose_splitters<2>(smem, v, p, L); break;
-    case 3: choose_splitters<3>(smem, v, p, L); break;
-    default: choose_splitters<4>(smem, v, p, L); break;
+    case 1: sort_sample_chunk<1>(smem, v, p, m, j); break;
+    case 2: sort_sample_chunk<2>(smem, v, p, m, j); break;
+    case 3: sort_sample_chunk<3>(smem, v, p, m, j); break;
+    default: sort_sample_chunk<4>(smem, v, p, m, j); break;
   }
+}
+
+template <int K>
+__device__ void select_splitters(const AutoView& v, const BucketPlan& p, uint32_t m, uint32_t j) {
+  constexpr uint32_t CH = spl_chunk(K);
+  const uint32_t ns = p.g - 1;
+  uint64_t* sk = reinterpret_cast<uint64_t*>(v.spl + p.spl_off + kDirBytes);
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + static_cast<size_t>(K) * ns);
+  if (m == 0) {
+    if (j == 0) {
+      for (uint32_t s = threadIdx.x; s < ns; s += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sk[k * ns + s] = ~0ull;
+        si[s] = ~0u;
+      }
+    }
+    return;
+  }
+  const uint32_t lo = j * CH;
+  if (lo >= m) return;
+  const uint32_t cnt = min(CH, m - lo);
+  const uint32_t chunks = (m + CH - 1) / CH;
+  const SmemTile<K> g = sample_tile<K>(v, p);
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const Elem<K> e = g.get(lo + i);
+    // binary searches in all other chunks in lockstep (independent loads)
+    uint32_t a[kSplChunks], b[kSplChunks];
+#pragma unroll
+    for (uint32_t q = 0; q < kSplChunks; ++q) {
+      a[q] = 0;
+      b[q] = (q < chunks && q != j) ? min(CH, m - q * CH) : 0u;
+    }
+    for (uint32_t w = CH; w > 0; w >>= 1) {  // at most log2(CH) + 1 halvings
+#pragma unroll
+      for (uint32_t q = 0; q < kSplChunks; ++q) {
+        if (a[q] < b[q]) {
+          const uint32_t mid = (a[q] + b[q]) >> 1;
+          if (elem_less<K>(g.get(q * CH + mid), e)) a[q] = mid + 1;
+          else b[q] = mid;
+        }
+      }
+    }
+    uint32_t r = i;
+#pragma unroll
+    for (uint32_t q = 0; q < kSplChunks; ++q) r += a[q];
+    // splitters s with floor((s+1) m / g) == r: s+1 in [ceil(r g / m), ceil((r+1) g / m))
+    const uint64_t s1 = (static_cast<uint64_t>(r) * p.g + m - 1) / m;
+    const uint64_t s2 = (static_cast<uint64_t>(r + 1) * p.g + m - 1) / m;
+    for (uint64_t t = s1 < 1 ? 1 : s1; t < s2 && t <= ns; ++t) {
+      const uint32_t sp = static_cast<uint32_t>(t - 1);
+#pragma unroll
+      for (int k = 0; k < K; ++k) sk[k * ns + sp] = e.k[k];
+      si[sp] = e.idx;
+    }
+  }
+}
+
+// (b) grid (W, kSplChunks): CTA (L-1, j) ranks the samples of chunk j of
+// bucket L and writes those that are splitters.
+__global__ void __launch_bounds__(1024)
+auto_spl_select_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
+  __shared__ uint32_t s_off[kMaxW + 2];
+  __shared__ BucketPlan p;
+  const AutoView& v = av;
+  const uint32_t L = blockIdx.x + 1, j = blockIdx.y;
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
+  __syncthreads();
+  if (p.g < 2) return;
+  const uint32_t m = min(v.hdr->samp_cnt[L], p.scap);
+  switch (p.K) {
+    case 1: select_splitters<1>(v, p, m, j); break;
+    case 2: select_splitters<2>(v, p, m, j); break;
+    case 3: select_splitters<3>(v, p, m, j); break;
+    default: select_splitters<4>(v, p, m, j); break;
+  }
+}
+
+// (c) one CTA per bucket: directory dir[b] = number of splitters whose first
+// byte is below b (splitters are sorted, so their first bytes never decrease).
+__global__ void __launch_bounds__(288)
+auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
+  __shared__ uint32_t s_off[kMaxW + 2];
+  __shared__ BucketPlan p;
+  const AutoView& v = av;
+  const uint32_t L = blockIdx.x + 1;
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
+  __syncthreads();
+  if (p.g < 2) return;
+  const uint32_t ns = p.g - 1, b = threadIdx.x;
+  if (b > 256) return;
+  uint16_t* dir = reinterpret_cast<uint16_t*>(v.spl + p.spl_off);
+  const uint64_t* sk0 = reinterpret_cast<const uint64_t*>(v.spl + p.spl_off + kDirBytes);
+  uint32_t lo = 0, hi = ns;  // first splitter with first byte >= b
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((sk0[mid] >> 56) < b) lo = mid + 1;
+    else hi = mid;
+  }
+  dir[b] = static_cast<uint16_t>(lo);
 }
 
 // ---------------------------------------------------------------------------
 // 3. partition
 // ---------------------------------------------------------------------------
-// Segment of the element (key[0..K), idx) of bucket plan p: the number of
-// splitters <= the element (splitters are sorted ascending).
-template <int K>
-__device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, const BucketPlan& p,
-                                                 const uint64_t (&key)[K], uint32_t idx) {
+// Per-bucket constants of the partition (shared memory, 32 bytes: two
+// vector loads).
+struct __align__(16) PartPlan {
+  uint32_t g, seg0, spl_off, cap;
+  uint64_t r64, r32;
+};
+
+// Key word k (big-endian, bytes past L zero) of word i, from its record.
+__device__ __forceinline__ uint64_t record_key(const uint8_t* rec, uint32_t W, uint32_t i, uint32_t L,
+                                               uint32_t k) {
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
+  return bswap64(__ldg(src + k)) & key_mask(L, k);
+}
+
+// Is splitter sp (whose first key word equals the element's) <= the element
+// (key words 1..K-1 read from the record, then the index)?  Multi-key ties
+// only: rare.
+__device__ __forceinline__ bool splitter_le_tie(const uint64_t* sk, const uint32_t* si, uint32_t ns,
+                                             uint32_t sp, uint32_t K, const uint8_t* rec,
+                                             uint32_t W, uint32_t i, uint32_t L) {
+  for (uint32_t k = 1; k < K; ++k) {
+    const uint64_t a = sk[k * ns + sp], b = record_key(rec, W, i, L, k);
+    if (a != b) return a < b;
+  }
+  return si[sp] <= i;
+}
+
+// Segment of word i (length L, K key words, first key word k0) in bucket
+// plan p: the number of splitters <= the element (keys, i), splitters sorted
+// ascending.  The first-byte directory narrows the search to [lo, hi]; every
+// lane of the warp takes the same number of halving steps (the warp's
+// largest range), so the search loop does not diverge.  All lanes call; a
+// lane with active == false gets p.seg0.
+__device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, const PartPlan& p, uint32_t K,
+                                                 uint64_t k0, bool active, const uint8_t* rec,
+                                                 uint32_t W, uint32_t i, uint32_t L) {
   const uint32_t ns = p.g - 1;
   const uint16_t* dir = reinterpret_cast<const uint16_t*>(tab + p.spl_off);
   const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + p.spl_off + kDirBytes);
   const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(K) * ns);
   // splitters below dir[c] have a smaller first byte (all <= the element),
-  // those from dir[c+1] on a larger one; search only between
-  const uint32_t c = static_cast<uint32_t>(key[0] >> 56);
-  uint32_t lo = dir[c], hi = dir[c + 1];  // answer in [lo, hi]
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;  // is splitter mid-1 <= element ?
-    const uint32_t s = mid - 1;
-    bool le = false, decided = false;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t a = sk[k * ns + s];
-      if (!decided && a != key[k]) {
-        le = a < key[k];
-        decided = true;
-      }
+  // those from dir[c+1] on a larger one
+  const uint32_t c = static_cast<uint32_t>(k0 >> 56);
+  uint32_t lo = 0, hi = 0;
+  if (active) {
+    lo = dir[c];
+    hi = dir[c + 1];
+  }
+  const uint32_t steps = __reduce_max_sync(0xffffffffu, 32u - __clz(hi - lo));
+  for (uint32_t t = 0; t < steps; ++t) {
+    if (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1, sp = mid - 1;  // is splitter mid-1 <= element ?
+      const uint64_t a = sk[sp];
+      bool le = a < k0;
+      if (a == k0) le = K == 1 ? si[sp] <= i : splitter_le_tie(sk, si, ns, sp, K, rec, W, i, L);
+      lo = le ? mid : lo;
+      hi = le ? hi : mid - 1;
     }
-    if (!decided) le = si[s] <= idx;
-    if (le) lo = mid;
-    else hi = mid - 1;
   }
   return p.seg0 + lo;
 }
 
-// Record words raw[0..K) (as loaded) of word i, length L -> big-endian masked
-// keys in key[0..K) and the word's segment.
-template <int K, int KW>
-__device__ __forceinline__ uint32_t classify(uint64_t (&key)[KW], uint32_t i, uint32_t L,
-                                             const BucketPlan& p, const uint8_t* tab) {
-  uint64_t kk[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    kk[k] = bswap64(key[k]) & key_mask(L, k);
-    key[k] = kk[k];
-  }
-  return p.g > 1 ? find_segment<K>(tab, p, kk, i) : p.seg0;
-}
+// Words per lane in flight per iteration of the partition loop.
+constexpr uint32_t kPartWords = 2;
 
-template <int KW>
 __global__ void __launch_bounds__(kPartThreads, 2)
 auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
                       uint32_t n_cap, const uint32_t* __restrict__ d_n, uint32_t W,
-                      const uint32_t* __restrict__ d_off, int retry_pass, Ws ws) {
+                      const uint32_t* __restrict__ d_off, int retry_pass, Ws ws, AutoView av) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ BucketPlan plans[kMaxW + 1];
+  __shared__ PartPlan plans[kMaxW + 1];
   __shared__ uint32_t s_off[kMaxW + 2];
-  const AutoView v = auto_view(ws, W);
+  const AutoView& v = av;
   if (retry_pass && v.hdr->retry == 0) return;
-  load_plans(plans, s_off, d_off, W, v.cap);
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x <= W) {
+    const BucketPlan bp = threadIdx.x ? plan_for(s_off, threadIdx.x, v.cap) : BucketPlan{};
+    plans[threadIdx.x] = PartPlan{bp.g, bp.seg0, bp.spl_off, bp.cap, bp.r64, bp.r32};
+  }
   // splitter table: staged in shared memory when it fits
   const uint32_t tb = v.hdr->spl_bytes;
   const uint8_t* tab = v.spl;
@@ -399,40 +519,33 @@ auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict
     const uint4* src = reinterpret_cast<const uint4*>(v.spl);
     uint4* dst = reinterpret_cast<uint4*>(smem);
     for (uint32_t i = threadIdx.x; i < tb / 16; i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
     tab = smem;
   }
+  __syncthreads();
   const uint32_t n = word_count(n_cap, d_n);
   const uint32_t lane = lane_id();
   bool overflow = false;
-  constexpr uint32_t kPartWords = PartWords<KW>::value;
   const uint32_t warps_total = gridDim.x * (blockDim.x / 32);
-  const uint32_t step = 32 * kPartWords;
+  constexpr uint32_t step = 32 * kPartWords;
   for (uint32_t base = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * step; base < n;
        base += warps_total * step) {
     uint32_t L[kPartWords], seg[kPartWords];
-    uint64_t key[kPartWords][KW];
+    uint64_t k0[kPartWords];
     // all loads first: kPartWords independent records per lane in flight
 #pragma unroll
     for (uint32_t u = 0; u < kPartWords; ++u) {
       const uint32_t i = base + u * 32 + lane;
       const uint32_t l = i < n ? len[i] : 0u;
       L[u] = l > W ? 0u : l;
-      const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
-#pragma unroll
-      for (int k = 0; k < KW; ++k) key[u][k] = L[u] ? __ldg(src + k) : 0ull;
+      k0[u] = L[u] ? __ldg(reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W)) : 0ull;
     }
 #pragma unroll
     for (uint32_t u = 0; u < kPartWords; ++u) {
       const uint32_t i = base + u * 32 + lane;
-      seg[u] = 0xFFFFFFFFu;
-      if (L[u]) {
-        const BucketPlan& p = plans[L[u]];
-        if (KW == 1 || p.K == 1) seg[u] = classify<1, KW>(key[u], i, L[u], p, tab);
-        else if (KW == 2 || p.K == 2) seg[u] = classify<(KW >= 2 ? 2 : 1), KW>(key[u], i, L[u], p, tab);
-        else if (KW == 3 || p.K == 3) seg[u] = classify<(KW >= 3 ? 3 : 1), KW>(key[u], i, L[u], p, tab);
-        else seg[u] = classify<KW, KW>(key[u], i, L[u], p, tab);
-      }
+      const PartPlan p = plans[L[u]];  // plans[0]: no segments
+      k0[u] = bswap64(k0[u]) & key_mask(L[u] ? L[u] : 1u, 0);
+      const uint32_t sg = find_segment(tab, p, keys_for_len(L[u]), k0[u], p.g > 1, rec, W, i, L[u]);
+      seg[u] = L[u] ? sg : 0xFFFFFFFFu;
     }
     uint32_t peers[kPartWords], first[kPartWords];
 #pragma unroll
@@ -446,15 +559,17 @@ auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict
     for (uint32_t u = 0; u < kPartWords; ++u) {
       const uint32_t f = __shfl_sync(0xffffffffu, first[u], __ffs(peers[u]) - 1);
       if (seg[u] == 0xFFFFFFFFu) continue;
+      const uint32_t i = base + u * 32 + lane;
       const uint32_t pos = f + __popc(peers[u] & lanemask_lt());
-      const BucketPlan& p = plans[L[u]];
+      const uint32_t K = keys_for_len(L[u]);
       uint32_t rc;
       uint64_t rb, ib;
       if (!retry_pass) {
         // optimistic layout: a pure function of the bucket plan
+        const PartPlan p = plans[L[u]];
         const uint32_t j = seg[u] - p.seg0;
         rc = p.cap;
-        rb = p.r64 + static_cast<uint64_t>(j) * p.cap * p.K;
+        rb = p.r64 + static_cast<uint64_t>(j) * p.cap * K;
         ib = p.r32 + static_cast<uint64_t>(j) * p.cap;
       } else {
         rc = v.rcap[seg[u]];
@@ -462,10 +577,9 @@ auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict
         ib = v.ibase[seg[u]];
       }
       if (pos < rc) {
-#pragma unroll
-        for (int k = 0; k < KW; ++k)
-          if (k < static_cast<int>(p.K)) v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = key[u][k];
-        v.area32[ib + pos] = base + u * 32 + lane;
+        v.area64[rb + pos] = k0[u];
+        for (uint32_t k = 1; k < K; ++k) v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = record_key(rec, W, i, L[u], k);
+        v.area32[ib + pos] = i;
       } else {
         overflow = true;
       }
@@ -484,9 +598,9 @@ __device__ __forceinline__ uint32_t exact_region(uint32_t x, uint32_t K) {
 }
 
 __global__ void __launch_bounds__(1024)
-auto_layout_kernel(uint32_t W, Ws ws) {
+auto_layout_kernel(uint32_t W, Ws ws, AutoView av) {
   __shared__ uint32_t tmp[1024 / 32 + 1];
-  const AutoView v = auto_view(ws, W);
+  const AutoView& v = av;
   const uint32_t G = v.hdr->G;
   const bool redo = v.hdr->overflow != 0;
   const uint32_t per = (G + blockDim.x - 1) / blockDim.x;
@@ -530,65 +644,23 @@ auto_layout_kernel(uint32_t W, Ws ws) {
 // ---------------------------------------------------------------------------
 // 5. segment sort + gather
 // ---------------------------------------------------------------------------
-// Padded shared-memory position: one spare slot per 16 elements keeps the
-// strided accesses of the merge rounds free of bank conflicts.
-__device__ __forceinline__ uint32_t pad16(uint32_t i) { return i + (i >> 4); }
+// Shared-memory planes of a resident segment (capacity elements each); a
+// one-key segment's radix counters (one row of 8-bit digit counters per
+// warp) and warp totals follow its planes.
+constexpr uint32_t kRxWarps = kSegThreads / 32;
+constexpr uint32_t kRxDigits = 256;
+constexpr size_t kRxHistBytes = kRxWarps * kRxDigits * sizeof(uint16_t) + kRxWarps * sizeof(uint32_t);
 
-// Elements per thread of the one-key (key, index) merge sort.
-template <int K> struct SegE { static constexpr int value = 8; };
+__host__ __device__ constexpr size_t seg_plane_elems(uint32_t K) { return auto_seg_cap(K); }
 
-__host__ __device__ constexpr size_t seg_plane_elems(uint32_t K) {
-  // padded capacity: pad16(cap - 1) + 1 rounded up to an even count
-  return (static_cast<size_t>(auto_seg_cap(K)) * 17 / 16 + 2) & ~static_cast<size_t>(1);
-}
-
-constexpr size_t kSegPlanesBytes = 104576;  // >= max over K of seg_plane_elems(K) x (8K + 4)
+// >= max over K of the planes (8K + 4 bytes per element), and the one-key
+// planes plus the radix counters (checked below)
+constexpr size_t kSegPlanesBytes = 106560;
 
 // One segment buffer per CTA (two CTAs per SM overlap each other's copies,
 // sorts and stores): barrier + planes.
 constexpr size_t kSegBufBytes = 16 + kSegPlanesBytes;
-__host__ __device__ constexpr size_t segsort_smem_bytes() {
-  return 128 + kSegBufBytes;  // alignment slack, buffer
-}
-
-template <int K>
-__device__ __forceinline__ Elem<K> elem_inf() {
-  Elem<K> e;
-#pragma unroll
-  for (int k = 0; k < K; ++k) e.k[k] = ~0ull;
-  e.idx = ~0u;
-  return e;
-}
-
-template <int K>
-__device__ __forceinline__ void cswap(Elem<K>& a, Elem<K>& b) {
-  if (elem_less<K>(b, a)) {
-    const Elem<K> t = a;
-    a = b;
-    b = t;
-  }
-}
-
-// Bitonic network on E registers (E a power of two), ascending.
-template <int K, int E>
-__device__ __forceinline__ void sort_regs(Elem<K> (&r)[E]) {
-#pragma unroll
-  for (int k = 2; k <= E; k <<= 1) {
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int j = i ^ (k - 1);
-      if (j > i && (i & (k >> 1)) == 0) cswap<K>(r[i], r[j]);
-    }
-#pragma unroll
-    for (int jj = k >> 2; jj > 0; jj >>= 1) {
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int j = i ^ jj;
-        if (j > i) cswap<K>(r[i], r[j]);
-      }
-    }
-  }
-}
+__host__ __device__ constexpr size_t segsort_smem_bytes() { return kSegBufBytes; }
 
 template <int K>
 __device__ __forceinline__ void write_word(uint32_t W, uint8_t* out_rec, uint32_t* out_perm,
@@ -605,71 +677,6 @@ __device__ __forceinline__ void write_word(uint32_t W, uint8_t* out_rec, uint32_
     for (uint32_t k = 0; k < KW; ++k) dst[k] = k < static_cast<uint32_t>(K) ? bswap64(e.k[k]) : 0ull;
   }
   out_perm[r] = e.idx;
-}
-
-// Sorts the c elements held unpadded in t (planes of seg_plane_elems(K)) and
-// writes them at output ranks ob.. .  Register sort of E elements per thread,
-// then merge-path rounds through padded shared memory.  Only the first
-// ceil(c / E) threads carry elements; positions at or past c read as +inf, so
-// the work follows c, not the capacity.
-template <int K, int E>
-__device__ void block_merge_sort_out(const SmemTile<K>& t, uint32_t c, uint32_t W, uint32_t ob,
-                                     uint8_t* out_rec, uint32_t* out_perm) {
-  const uint32_t tid = threadIdx.x;
-  const uint32_t active = (c + E - 1) / E;
-  const bool act = tid < active;
-  Elem<K> r[E];
-  // thread tid takes positions tid*E .. tid*E+E-1, so the +inf padding sits
-  // at the end of the last active thread's run only
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const uint32_t i = tid * E + j;
-    r[j] = (act && i < c) ? t.get(i) : elem_inf<K>();
-  }
-  if (act) sort_regs<K, E>(r);
-  auto get = [&](uint32_t i) { return i < c ? t.get(pad16(i)) : elem_inf<K>(); };
-  for (uint32_t R = E; R < c; R <<= 1) {
-    __syncthreads();  // previous readers are done with shared memory
-    if (act) {
-#pragma unroll
-      for (int j = 0; j < E; ++j)
-        if (tid * E + j < c) t.put(pad16(tid * E + j), r[j]);
-    }
-    __syncthreads();
-    if (act) {
-      const uint32_t my = tid * E, ps = my & ~(2 * R - 1), d = my - ps;
-      uint32_t lo = d > R ? d - R : 0u, hi = min(d, R);
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (elem_less<K>(get(ps + mid), get(ps + R + d - 1 - mid))) lo = mid + 1;
-        else hi = mid;
-      }
-      uint32_t ia = ps + lo, ib = ps + R + (d - lo);
-      const uint32_t ae = ps + R, be = ps + 2 * R;
-      Elem<K> ha = ia < ae ? get(ia) : elem_inf<K>();
-      Elem<K> hb = ib < be ? get(ib) : elem_inf<K>();
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const bool ta = elem_less<K>(ha, hb);
-        r[j] = ta ? ha : hb;
-        if (ta) {
-          ++ia;
-          ha = ia < ae ? get(ia) : elem_inf<K>();
-        } else {
-          ++ib;
-          hb = ib < be ? get(ib) : elem_inf<K>();
-        }
-      }
-    }
-  }
-  if (act) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const uint32_t pos = tid * E + j;
-      if (pos < c) write_word<K>(W, out_rec, out_perm, ob + pos, r[j]);
-    }
-  }
-  __syncthreads();  // shared memory is reused by the next segment
 }
 
 // A segment larger than shared memory (only after a retry, whose region is
@@ -755,245 +762,183 @@ __device__ bool maybe_prefetch(uint8_t* buf, const AutoView& v, uint32_t seg, ui
   return true;
 }
 
-// ---- one-word composite elements -----------------------------------------
-// A one-key segment whose keys (without their zero tail bytes) span at most
-// kb bits and whose indices fit ib bits, with kb + ib <= 64, sorts as single
-// uint64 values ((key >> shift) - kmin) << ib | idx: the integer order of the
-// composites is the (key, index) order.
-
-__device__ __forceinline__ void cswap64(uint64_t& a, uint64_t& b) {
-  const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-  a = lo;
-  b = hi;
-}
-
-template <int E>
-__device__ __forceinline__ void sort_regs64(uint64_t (&r)[E]) {
-#pragma unroll
-  for (int k = 2; k <= E; k <<= 1) {
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int j = i ^ (k - 1);
-      if (j > i && (i & (k >> 1)) == 0) cswap64(r[i], r[j]);
-    }
-#pragma unroll
-    for (int jj = k >> 2; jj > 0; jj >>= 1) {
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int j = i ^ jj;
-        if (j > i) cswap64(r[i], r[j]);
-      }
-    }
+// ---- one-key segments: LSD radix sort -----------------------------------
+// A one-key segment (words of at most 8 letters) orders its elements by the
+// integer (key - kmin) * 2^ib + idx, where key is the word's key without its
+// zero tail bytes, kmin the smallest such key in the segment and ib the bit
+// width of the largest index: that integer order is the (key, index) order.
+// It spans kb + ib bits, kb the width of kmax - kmin.  An item is one uint64
+// when kb + ib <= 64 (Item64), else a (key - kmin, idx) pair (Item96).  The
+// sort is least-significant-digit first, 8 bits per pass, each pass stable.
+struct Item64 {
+  uint64_t v;
+  __device__ uint32_t digit(uint32_t s, uint32_t) const { return static_cast<uint32_t>(v >> s) & 255u; }
+};
+struct Item96 {
+  uint64_t k;
+  uint32_t i;
+  // bits [s, s+8) of k * 2^ib + i
+  __device__ uint32_t digit(uint32_t s, uint32_t ib) const {
+    if (s + 8 <= ib) return (i >> s) & 255u;
+    if (s >= ib) return static_cast<uint32_t>(k >> (s - ib)) & 255u;
+    return ((i >> s) | static_cast<uint32_t>(k << (ib - s))) & 255u;
   }
-}
-
-// Register bitonic sort of N = E * blockDim.x positions, blocked layout:
-// thread t holds positions t*E .. t*E+E-1 in r[].  All-ascending form: for
-// each block size k the first step pairs i with i ^ (k-1), the next ones pair
-// i with i ^ j (j = k/4 .. 1); the lower position keeps the smaller value.
-// A partner in the same thread is compared in registers, one in the same warp
-// through __shfl_xor_sync, one in another warp through shared memory.  Every
-// compare-exchange of a step is independent, so all threads and warps work in
-// every step.  Ops supplies the element order, the warp shuffle and the
-// shared-memory exchange slots (padded positions).
-
-// Plain uint64 composites; exchange slots in plane[].
-struct U64Ops {
-  using T = uint64_t;
-  uint64_t* plane;
-  __device__ static bool less(uint64_t a, uint64_t b) { return a < b; }
-  __device__ static uint64_t shfl(uint64_t x, uint32_t m) { return __shfl_xor_sync(0xffffffffu, x, m); }
-  __device__ static uint64_t inf() { return ~0ull; }
-  __device__ void st(uint32_t i, uint64_t v) const { plane[pad16(i)] = v; }
-  __device__ uint64_t ld(uint32_t i) const { return plane[pad16(i)]; }
+};
+struct Store64 {
+  uint64_t* a;
+  __device__ Item64 load(uint32_t p) const { return Item64{a[p]}; }
+  __device__ void store(uint32_t p, const Item64& x) const { a[p] = x.v; }
+};
+struct Store96 {
+  uint64_t* k;
+  uint32_t* i;
+  __device__ Item96 load(uint32_t p) const { return Item96{k[p], i[p]}; }
+  __device__ void store(uint32_t p, const Item96& x) const {
+    k[p] = x.k;
+    i[p] = x.i;
+  }
 };
 
-// (key words, index) elements; exchange slots in the tile's planes.
-template <int K>
-struct ElemOps {
-  using T = Elem<K>;
-  SmemTile<K> t;
-  __device__ static bool less(const Elem<K>& a, const Elem<K>& b) { return elem_less<K>(a, b); }
-  __device__ static Elem<K> shfl(const Elem<K>& x, uint32_t m) {
-    Elem<K> y;
+// Lanes of the warp holding the same 8-bit digit d (one ballot per bit).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int k = 0; k < K; ++k) y.k[k] = __shfl_xor_sync(0xffffffffu, x.k[k], m);
-    y.idx = __shfl_xor_sync(0xffffffffu, x.idx, m);
-    return y;
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t m = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? m : ~m;
   }
-  __device__ static Elem<K> inf() { return elem_inf<K>(); }
-  __device__ void st(uint32_t i, const Elem<K>& v) const { t.put(pad16(i), v); }
-  __device__ Elem<K> ld(uint32_t i) const { return t.get(pad16(i)); }
-};
-
-template <typename Ops, int M, int E>
-__device__ __forceinline__ void reg_step(typename Ops::T (&r)[E]) {
-  if constexpr (M < E) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      constexpr int m = M;
-      const int q = j ^ m;
-      if (q > j && Ops::less(r[q], r[j])) {
-        const typename Ops::T x = r[j];
-        r[j] = r[q];
-        r[q] = x;
-      }
-    }
-  }
+  return peers;
 }
 
-template <typename Ops, int E>
-__device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops& ops, uint32_t mask) {
-  using T = typename Ops::T;
-  constexpr uint32_t LE = E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4;
-  const uint32_t tid = threadIdx.x;
-  const uint32_t lane_mask = mask >> LE;
-  if (mask < E) {
-    // in registers: masks are the flips 1, 3, 7, 15 or the cleaners 1, 2, 4, 8
-    switch (mask) {
-      case 1: reg_step<Ops, 1, E>(r); break;
-      case 2: reg_step<Ops, 2, E>(r); break;
-      case 3: reg_step<Ops, 3, E>(r); break;
-      case 4: reg_step<Ops, 4, E>(r); break;
-      case 7: reg_step<Ops, 7, E>(r); break;
-      case 8: reg_step<Ops, 8, E>(r); break;
-      default: reg_step<Ops, 15, E>(r); break;
-    }
-  } else if (lane_mask < 32) {
-    // across lanes of one warp; my position is the upper one of its pair when
-    // the highest bit of the lane part of the mask is set in my lane
-    const uint32_t top = 1u << (31 - __clz(lane_mask));
-    const bool keep_small = (tid & top) == 0;
-    if ((mask & (E - 1)) == 0) {
-      // cleaner step: the partner holds the same slot j
+// Exclusive prefix sums of the per-warp digit counts hist[w][d] in (digit,
+// warp) order, written back in place: afterwards hist[w][d] is the first
+// output position of warp w's items with digit d.  Thread t scans digit t/2
+// for warps 8(t%2) .. 8(t%2)+7, so thread order is (digit, warp) order.
+__device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp_tmp) {
+  static_assert(kSegThreads * 8 == kRxWarps * kRxDigits, "eight counters per thread");
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  uint16_t* h = hist + ((t & 1u) * 8) * kRxDigits + (t >> 1);  // entry (warp 8(t%2) + k, digit t/2)
+  uint32_t v[8], sum = 0;
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const T other = Ops::shfl(r[j], lane_mask);
-        if (Ops::less(other, r[j]) == keep_small) r[j] = other;
-      }
-    } else {
-      // flip step (mask = k - 1): slot j pairs with the partner's slot E-1-j.
-      // Slots j and E-1-j are exchanged together: sending slot E-1-j delivers
-      // the partner's value for my slot j, sending slot j the one for E-1-j.
-#pragma unroll
-      for (int j = 0; j < E / 2; ++j) {
-        const T for_j = Ops::shfl(r[E - 1 - j], lane_mask);
-        const T for_m = Ops::shfl(r[j], lane_mask);
-        if (Ops::less(for_j, r[j]) == keep_small) r[j] = for_j;
-        if (Ops::less(for_m, r[E - 1 - j]) == keep_small) r[E - 1 - j] = for_m;
-      }
-    }
-  } else {
-    // across warps: exchange through shared memory
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < E; ++j) ops.st(tid * E + j, r[j]);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const uint32_t i = tid * E + j, pi = i ^ mask;
-      const T other = ops.ld(pi);
-      if (Ops::less(other, r[j]) == (i < pi)) r[j] = other;
-    }
+  for (int k = 0; k < 8; ++k) {
+    v[k] = h[k * kRxDigits];
+    sum += v[k];
   }
-}
-
-// Sorts the first c values (read by get(i), unpadded) with a register bitonic
-// network of E per thread and hands them to sink(pos, value).  Needs
-// c <= E * blockDim.x; ops' exchange slots must hold pad16(E*blockDim.x - 1) + 1.
-template <typename Ops, int E, typename Get, typename Sink>
-__device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
-  using T = typename Ops::T;
-  const uint32_t tid = threadIdx.x;
-  T r[E];
+  const uint32_t inc = warp_inclusive_scan(sum);
+  if (lane == 31) warp_tmp[warp] = inc;
+  __syncthreads();
+  // lane q holds warp q's total: exclusive prefix at my warp
+  const uint32_t mine = lane < kRxWarps ? warp_tmp[lane] : 0u;
+  const uint32_t upto = warp_inclusive_scan(mine);
+  uint32_t run = __shfl_sync(0xffffffffu, upto - mine, warp) + inc - sum;
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const uint32_t i = tid * E + j;
-    r[j] = i < c ? get(i) : Ops::inf();
+  for (int k = 0; k < 8; ++k) {
+    h[k * kRxDigits] = static_cast<uint16_t>(run);
+    run += v[k];
   }
-  uint32_t N = 2;
-  while (N < c) N <<= 1;
-  if (N < E) N = E;
-  for (uint32_t k = 2; k <= N; k <<= 1) {
-    bitonic_step<Ops, E>(r, ops, k - 1);
-    for (uint32_t j = k >> 2; j > 0; j >>= 1) bitonic_step<Ops, E>(r, ops, j);
-  }
-#pragma unroll
-  for (int j = 0; j < E; ++j)
-    if (tid * E + j < c) sink(tid * E + j, r[j]);
   __syncthreads();
 }
 
-// LSD radix sort of c uint64 values on their low `bits` bits, 8 bits per
-// pass, stable: each pass counts digits per warp over warp-contiguous ranges
-// (warp w owns positions [w S, (w+1) S)), scans the (digit, warp) counts in
-// digit-major order, then every warp writes its values in position order to
-// base[digit][warp] + (earlier equal digits in the warp).  A and B hold c
-// values each (A the input), hist 16 x 256 counters (one row per warp of a
-// 512-thread block).  Returns the array holding the result.
-constexpr uint32_t kRadixWarps = kSegThreads / 32;
-constexpr uint32_t kRadixMaxC = 5504;  // A, B and hist fit one segment buffer
-
-__device__ uint64_t* block_radix_u64(uint64_t* A, uint64_t* B, uint32_t* hist, uint32_t c,
-                                     uint32_t bits) {
+// Stable LSD radix sort of c items, held in registers: warp w owns positions
+// [w S, w S + S) (S = ceil(c / warps) rounded up to 32), lane l holds
+// position w S + 32 j + l in x[j], read through get(p).  Each pass ranks the
+// items of a warp in position order (running per-warp digit counters
+// hist[w][*] plus the lanes below with the same digit), scans the counters,
+// and scatters every item to its new position in the store.  The sorted items
+// end in st[0, c).
+template <typename It, typename St, int E, typename Get>
+__device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t bits, uint32_t ib,
+                                                 St st, uint16_t* hist, uint32_t* warp_tmp) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint32_t S = ((c + kRadixWarps - 1) / kRadixWarps + 31) / 32 * 32;
-  const uint32_t w0 = min(c, warp * S), w1 = min(c, w0 + S);
-  uint32_t* row = hist + warp * 256;
-  uint64_t* src = A;
-  uint64_t* dst = B;
-  for (uint32_t shift = 0; shift < bits; shift += 8) {
-    for (uint32_t i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    // 1. counts per (warp, digit)
-    for (uint32_t b = w0; b < w1; b += 32) {
-      const uint32_t pos = b + lane;
-      const bool valid = pos < w1;
-      const uint32_t d = valid ? static_cast<uint32_t>(src[pos] >> shift) & 255u : 256u + lane;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid && lane == __ffs(peers) - 1) row[d] += __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    // 2. exclusive scan in digit-major, warp-minor order (entry d * 16 + w)
-    {
-      __shared__ uint32_t tmp[kSegThreads / 32 + 1];
-      constexpr uint32_t per = kRadixWarps * 256 / kSegThreads;  // 8 entries per thread
-      uint32_t v[per], sum = 0;
+  const uint32_t S = ((c + kRxWarps - 1) / kRxWarps + 31) & ~31u;
+  const uint32_t w0 = warp * S, lt = lanemask_lt();
+  uint16_t* row = hist + warp * kRxDigits;
+  It x[E];
 #pragma unroll
-      for (uint32_t k = 0; k < per; ++k) {
-        const uint32_t e = threadIdx.x * per + k, d = e / kRadixWarps, w = e % kRadixWarps;
-        v[k] = hist[w * 256 + d];
-        sum += v[k];
-      }
-      uint32_t tot;
-      uint32_t run = block_exclusive_scan(sum, tmp, &tot);
+  for (int j = 0; j < E; ++j)
+    if (static_cast<uint32_t>(j) * 32 < S && w0 + j * 32 + lane < c) x[j] = get(w0 + j * 32 + lane);
+  // every item is read before the first pass scatters into the store
+  __syncthreads();
+  uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
+  for (uint32_t s = 0; s < bits; s += 8) {
+    for (uint32_t i = lane; i < kRxDigits; i += 32) row[i] = 0;
+    __syncwarp();
 #pragma unroll
-      for (uint32_t k = 0; k < per; ++k) {
-        const uint32_t e = threadIdx.x * per + k, d = e / kRadixWarps, w = e % kRadixWarps;
-        hist[w * 256 + d] = run;
-        run += v[k];
+    for (int j = 0; j < E; ++j) {
+      if (static_cast<uint32_t>(j) * 32 < S) {  // warp-uniform
+        const bool valid = w0 + j * 32 + lane < c;
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+        const uint32_t d = x[j].digit(s, ib);
+        const uint32_t peers = digit_peers(d) & vm;
+        const uint32_t leader = (__ffs(peers) - 1) & 31u;
+        uint32_t base = 0;
+        if (valid && lane == leader) {
+          base = row[d];
+          row[d] = static_cast<uint16_t>(base + __popc(peers));
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const uint32_t r = base + __popc(peers & lt);
+        if (j & 1) rk[j / 2] |= r << 16;
+        else rk[j / 2] = r;
+        __syncwarp();
       }
     }
     __syncthreads();
-    // 3. stable scatter
-    for (uint32_t b = w0; b < w1; b += 32) {
-      const uint32_t pos = b + lane;
-      const bool valid = pos < w1;
-      const uint64_t x = valid ? src[pos] : 0ull;
-      const uint32_t d = valid ? static_cast<uint32_t>(x >> shift) & 255u : 256u + lane;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid) dst[row[d] + __popc(peers & lanemask_lt())] = x;
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) row[d] += __popc(peers);
-      __syncwarp();
+    scan_digit_counts(hist, warp_tmp);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if (static_cast<uint32_t>(j) * 32 < S && w0 + j * 32 + lane < c) {
+        const uint32_t r = (j & 1) ? rk[j / 2] >> 16 : rk[j / 2] & 0xffffu;
+        st.store(row[x[j].digit(s, ib)] + r, x[j]);
+      }
     }
     __syncthreads();
-    uint64_t* t = src;
-    src = dst;
-    dst = t;
+    if (s + 8 < bits) {
+#pragma unroll
+      for (int j = 0; j < E; ++j)
+        if (static_cast<uint32_t>(j) * 32 < S && w0 + j * 32 + lane < c) x[j] = st.load(w0 + j * 32 + lane);
+    }
   }
-  return src;
+}
+
+// Sorts the segment's items (converted from the key and index planes, which
+// are then reused as the item store) and writes the output records.  The
+// buffer comes as an offset into dynamic shared memory, so that every access
+// compiles to a shared-memory instruction.  Not inlined: the caller's segment
+// loop keeps its own state live, and the items need the registers.
+template <typename It, int E>
+__device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, uint32_t shift, uint64_t k0,
+                                      uint32_t kb, uint32_t ib, uint32_t W, uint32_t ob,
+                                      uint8_t* out_rec, uint32_t* out_perm) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  constexpr uint32_t C = auto_seg_cap(1);
+  uint64_t* kp = reinterpret_cast<uint64_t*>(smem_raw + buf_off);
+  uint32_t* ip = reinterpret_cast<uint32_t*>(kp + C);
+  uint16_t* hist = reinterpret_cast<uint16_t*>(ip + C);
+  uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
+  if constexpr (sizeof(It) == sizeof(Item64)) {
+    auto get = [=](uint32_t p) { return Item64{(((kp[p] >> shift) - k0) << ib) | ip[p]}; };
+    radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp);
+    const uint64_t imask = (1ull << ib) - 1;
+    for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
+      const uint64_t v = kp[r];
+      Elem<1> e;
+      e.k[0] = ((v >> ib) + k0) << shift;
+      e.idx = static_cast<uint32_t>(v & imask);
+      write_word<1>(W, out_rec, out_perm, ob + r, e);
+    }
+  } else {
+    auto get = [=](uint32_t p) { return Item96{(kp[p] >> shift) - k0, ip[p]}; };
+    radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp);
+    for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
+      Elem<1> e;
+      e.k[0] = (kp[r] + k0) << shift;
+      e.idx = ip[r];
+      write_word<1>(W, out_rec, out_perm, ob + r, e);
+    }
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ uint64_t warp_min64(uint64_t x) {
@@ -1032,16 +977,18 @@ __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uin
   __syncthreads();
 }
 
-// One-key segment of length-L words resident in buf: composite sort when the
-// key span and index width fit 64 bits, else the (key, index) merge sort.
-__device__ void sort_resident_k1(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c,
-                                 uint32_t L, uint32_t W, uint8_t* out_rec, uint32_t* out_perm) {
-  __shared__ uint64_t red[3][kSegThreads / 32];
+// One-key segment of length-L words resident in buf: find kmin, kmax and the
+// largest index, then radix-sort the (key - kmin, index) items.
+__device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
+                                 uint32_t seg, uint32_t c, uint32_t L, uint32_t W, uint8_t* out_rec,
+                                 uint32_t* out_perm) {
   __shared__ uint64_t s_kmin;
   __shared__ uint32_t s_kb, s_ib;
+  constexpr uint32_t C = auto_seg_cap(1);
   uint64_t* kp = reinterpret_cast<uint64_t*>(buf + 16);
-  const uint32_t C = static_cast<uint32_t>(seg_plane_elems(1));
   uint32_t* ip = reinterpret_cast<uint32_t*>(kp + C);
+  // per-warp partial results in the (not yet used) radix counter area
+  uint64_t (*red)[kSegThreads / 32] = reinterpret_cast<uint64_t (*)[kSegThreads / 32]>(ip + C);
   const uint32_t shift = 64 - 8 * L;  // L <= 8: the low 64-8L key bits are zero
   uint64_t kmin = ~0ull, kmax = 0, imax = 0;
   for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
@@ -1075,67 +1022,33 @@ __device__ void sort_resident_k1(uint8_t* buf, const AutoView& v, uint32_t seg, 
   const uint32_t kb = s_kb, ib = s_ib;
   const uint64_t k0 = s_kmin;
   const uint32_t ob = v.outbase[seg];
+  const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);
   if (kb + ib <= 64) {
-    for (uint32_t i = threadIdx.x; i < c; i += blockDim.x)
-      kp[i] = (((kp[i] >> shift) - k0) << ib) | ip[i];
-    __syncthreads();
-    const uint64_t imask = (1ull << ib) - 1;
-    auto sink = [&](uint32_t pos, uint64_t x) {
-      Elem<1> e;
-      e.k[0] = ((x >> ib) + k0) << shift;
-      e.idx = static_cast<uint32_t>(x & imask);
-      write_word<1>(W, out_rec, out_perm, ob + pos, e);
-    };
-    if (c <= kRadixMaxC) {
-      // A = composites over the key plane; B and the counters reuse the (now
-      // dead) rest of the buffer
-      uint64_t* B = kp + kRadixMaxC;
-      uint32_t* hist = reinterpret_cast<uint32_t*>(kp + 2 * kRadixMaxC);
-      const uint64_t* res = block_radix_u64(kp, B, hist, c, kb + ib);
-      for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) sink(r, res[r]);
-      __syncthreads();
-      return;
-    }
-    const U64Ops ops{kp};
-    auto get = [&](uint32_t i) { return kp[i]; };
-    // reads happen before the first exchange writes (each step syncs first)
-    if (c <= 4 * blockDim.x) block_sort<U64Ops, 4>(ops, c, get, sink);
-    else if (c <= 8 * blockDim.x) block_sort<U64Ops, 8>(ops, c, get, sink);
-    else block_sort<U64Ops, 16>(ops, c, get, sink);
+    if (c <= 4 * kSegThreads) k1_radix<Item64, 4>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
+    else if (c <= 8 * kSegThreads) k1_radix<Item64, 8>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
+    else k1_radix<Item64, 16>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
   } else {
-    SmemTile<1> t;
-    t.k[0] = kp;
-    t.idx = ip;
-    const ElemOps<1> ops{t};
-    auto get = [&](uint32_t i) { return t.get(i); };
-    auto sink = [&](uint32_t pos, const Elem<1>& e) { write_word<1>(W, out_rec, out_perm, ob + pos, e); };
-    if (c <= 4 * blockDim.x) block_sort<ElemOps<1>, 4>(ops, c, get, sink);
-    else if (c <= 8 * blockDim.x) block_sort<ElemOps<1>, 8>(ops, c, get, sink);
-    else {
-      // rare: a wide-key segment above 4096 words
-      bitonic_flip<1>(t, c);
-      __syncthreads();
-      for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) write_word<1>(W, out_rec, out_perm, ob + r, t.get(r));
-      __syncthreads();
-    }
+    if (c <= 4 * kSegThreads) k1_radix<Item96, 4>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
+    else if (c <= 8 * kSegThreads) k1_radix<Item96, 8>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
+    else k1_radix<Item96, 16>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
   }
 }
 
 // Persistent CTAs (two per SM) walk the segments: bulk-copy the segment into
 // shared memory, sort, write the output records and permutation.
 __global__ void __launch_bounds__(kSegThreads, 2)
-auto_segsort_kernel(uint32_t W, Ws ws, uint8_t* __restrict__ out_rec,
+auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_rec,
                     uint32_t* __restrict__ out_perm) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  uint8_t* buf = align128(smem_raw);
+  uint8_t* buf = smem_raw;  // 16-byte aligned: barrier, then the planes
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf);
-  const AutoView v = auto_view(ws, W);
-  const uint32_t G = v.hdr->G;
+  const AutoView& v = av;  // kernel parameter: read from the constant bank
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
   }
   __syncthreads();
+  const uint32_t G = v.hdr->G;
   uint32_t phase = 0;
   for (uint32_t seg = blockIdx.x; seg < G; seg += gridDim.x) {
     const uint32_t c = seg_count(v, seg);
@@ -1168,7 +1081,7 @@ auto_segsort_kernel(uint32_t W, Ws ws, uint8_t* __restrict__ out_rec,
       return;
     }
     switch (K) {
-      case 1: sort_resident_k1(buf, v, seg, c, L, W, out_rec, out_perm); break;
+      case 1: sort_resident_k1(smem_raw, buf, v, seg, c, L, W, out_rec, out_perm); break;
       case 2: sort_resident<2>(buf, v, seg, c, W, out_rec, out_perm); break;
       case 3: sort_resident<3>(buf, v, seg, c, W, out_rec, out_perm); break;
       default: sort_resident<4>(buf, v, seg, c, W, out_rec, out_perm); break;
@@ -1186,9 +1099,9 @@ constexpr uint32_t kHistThreads = 256;
 // per block.
 __global__ void __launch_bounds__(kHistThreads)
 auto_hist_kernel(const uint8_t* __restrict__ len, uint32_t n_cap, const uint32_t* __restrict__ d_n,
-                 uint32_t W, Ws ws) {
+                 uint32_t W, Ws ws, AutoView av) {
   __shared__ uint32_t cnt[kBins][kHistThreads];
-  const AutoView v = auto_view(ws, W);
+  const AutoView& v = av;
   for (uint32_t L = 0; L < kBins; ++L) cnt[L][threadIdx.x] = 0;
   const uint32_t n = word_count(n_cap, d_n);
   bool bad_zero = false, bad_long = false;
@@ -1237,9 +1150,9 @@ auto_hist_kernel(const uint8_t* __restrict__ len, uint32_t n_cap, const uint32_t
 
 // Bucket offsets off[L] (words shorter than L) from the totals; also resets
 // the per-call state of the sample sort.
-__global__ void auto_offsets_kernel(uint32_t W, Ws ws, uint32_t* __restrict__ off) {
+__global__ void auto_offsets_kernel(uint32_t W, Ws ws, AutoView av, uint32_t* __restrict__ off) {
   __shared__ uint32_t tot[kBins];
-  const AutoView v = auto_view(ws, W);
+  const AutoView& v = av;
   const uint32_t L = threadIdx.x;
   if (L < kBins) tot[L] = (L >= 1 && L <= W) ? v.hdr->total[L] : 0u;
   __syncthreads();
@@ -1259,36 +1172,26 @@ __global__ void auto_offsets_kernel(uint32_t W, Ws ws, uint32_t* __restrict__ of
 static_assert(seg_plane_elems(1) * 12 <= kSegPlanesBytes && seg_plane_elems(2) * 20 <= kSegPlanesBytes &&
                   seg_plane_elems(3) * 28 <= kSegPlanesBytes && seg_plane_elems(4) * 36 <= kSegPlanesBytes,
               "segment planes exceed the shared-memory budget");
-static_assert(16 * kSegThreads >= 8192, "composite E x threads must cover the segment capacity");
-static_assert((2 * kRadixMaxC * 8 + kRadixWarps * 256 * 4) <= kSegPlanesBytes,
-              "radix buffers exceed the segment buffer");
-static_assert(kRadixMaxC * 8 <= seg_plane_elems(1) * 8,
-              "the composite input must lie inside the key plane");
-static_assert(2 * (segsort_smem_bytes() + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");
+static_assert(16 * kSegThreads >= auto_seg_cap(1), "16 radix items per thread cover a one-key segment");
+static_assert(auto_seg_cap(1) * 12 + kRxHistBytes <= kSegPlanesBytes,
+              "one-key planes and radix counters exceed the segment buffer");
+static_assert(3 * kRxWarps * 8 <= kRxHistBytes, "reduction scratch fits the radix counters");
+// two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
+// a few scalars; ptxas -v reports it) + 1 KB reserved each
+static_assert(2 * (segsort_smem_bytes() + 256 + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");
 
 int g_sm_count = 0;
 
-template <int KW>
-cudaError_t launch_partition(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
-                             const uint32_t* d_n, uint32_t W, const uint32_t* d_off, const Ws& ws,
-                             int retry, cudaStream_t s) {
+cudaError_t partition(const uint8_t* rec, const uint8_t* len, uint32_t n_cap, const uint32_t* d_n,
+                      uint32_t W, const uint32_t* d_off, const Ws& ws, const AutoView& v, int retry,
+                      cudaStream_t s) {
   static size_t set = 0;
-  cudaError_t e = ensure_smem(auto_partition_kernel<KW>, kSplSmem, &set);
+  cudaError_t e = ensure_smem(auto_partition_kernel, kSplSmem, &set);
   if (e != cudaSuccess) return e;
   const uint32_t grid = static_cast<uint32_t>(g_sm_count) * 2;
-  BSORT_LAUNCH(retry ? "auto_partition_retry" : "auto_partition", auto_partition_kernel<KW>, grid,
-               kPartThreads, kSplSmem, s, rec, len, n_cap, d_n, W, d_off, retry, ws);
+  BSORT_LAUNCH(retry ? "auto_partition_retry" : "auto_partition", auto_partition_kernel, grid,
+               kPartThreads, kSplSmem, s, rec, len, n_cap, d_n, W, d_off, retry, ws, v);
   return cudaGetLastError();
-}
-
-cudaError_t partition(const uint8_t* rec, const uint8_t* len, uint32_t n_cap, const uint32_t* d_n,
-                      uint32_t W, const uint32_t* d_off, const Ws& ws, int retry, cudaStream_t s) {
-  switch (W / 8) {
-    case 1: return launch_partition<1>(rec, len, n_cap, d_n, W, d_off, ws, retry, s);
-    case 2: return launch_partition<2>(rec, len, n_cap, d_n, W, d_off, ws, retry, s);
-    case 3: return launch_partition<3>(rec, len, n_cap, d_n, W, d_off, ws, retry, s);
-    default: return launch_partition<4>(rec, len, n_cap, d_n, W, d_off, ws, retry, s);
-  }
 }
 
 }  // namespace
@@ -1304,8 +1207,7 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
                         uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {
   static size_t split_set = 0, seg_set = 0;
-  const size_t split_smem = 16384 * 12;  // max over K of auto_sample_max(K) x (8K + 4)
-  cudaError_t e = ensure_smem(auto_splitter_kernel, split_smem, &split_set);
+  cudaError_t e = ensure_smem(auto_spl_sort_kernel, kSplSortSmem, &split_set);
   if (e == cudaSuccess) e = ensure_smem(auto_segsort_kernel, segsort_smem_bytes(), &seg_set);
   if (e != cudaSuccess) return e;
   if (g_sm_count == 0) {
@@ -1315,23 +1217,28 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
     if (g_sm_count <= 0) g_sm_count = 148;
   }
   const uint32_t samples = n_cap / kAutoSampleEvery + 1;
-  // phase 2 counts: totals per length, then bucket offsets
+  // the workspace view, computed once here and passed to every kernel
   const AutoView v = auto_view(ws, W);
+  // phase 2 counts: totals per length, then bucket offsets
   e = cudaMemsetAsync(v.hdr->total, 0, sizeof(v.hdr->total), s);
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_hist", auto_hist_kernel, static_cast<uint32_t>(g_sm_count) * 4, kHistThreads,
-               0, s, len, n_cap, d_n, W, ws);
-  BSORT_LAUNCH("auto_offsets", auto_offsets_kernel, 1, 64, 0, s, W, ws, d_off);
+               0, s, len, n_cap, d_n, W, ws, v);
+  BSORT_LAUNCH("auto_offsets", auto_offsets_kernel, 1, 64, 0, s, W, ws, v, d_off);
   BSORT_LAUNCH("auto_sample", auto_sample_kernel, (samples + 255) / 256, 256, 0, s, rec, len,
-               n_cap, d_n, W, d_off, ws);
-  BSORT_LAUNCH("auto_splitters", auto_splitter_kernel, W, 1024, split_smem, s, d_off, W, ws);
-  e = partition(rec, len, n_cap, d_n, W, d_off, ws, 0, s);
+               n_cap, d_n, W, d_off, ws, v);
+  BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, s,
+               d_off, W, ws, v);
+  BSORT_LAUNCH("auto_spl_select", auto_spl_select_kernel, dim3(W, kSplChunks), 1024, 0, s, d_off, W,
+               ws, v);
+  BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, W, 288, 0, s, d_off, W, ws, v);
+  e = partition(rec, len, n_cap, d_n, W, d_off, ws, v, 0, s);
   if (e != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_layout", auto_layout_kernel, 1, 1024, 0, s, W, ws);
-  e = partition(rec, len, n_cap, d_n, W, d_off, ws, 1, s);
+  BSORT_LAUNCH("auto_layout", auto_layout_kernel, 1, 1024, 0, s, W, ws, v);
+  e = partition(rec, len, n_cap, d_n, W, d_off, ws, v, 1, s);
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_segsort", auto_segsort_kernel, static_cast<uint32_t>(g_sm_count) * 2,
-               kSegThreads, segsort_smem_bytes(), s, W, ws, out_rec, out_perm);
+               kSegThreads, segsort_smem_bytes(), s, W, ws, v, out_rec, out_perm);
   return cudaGetLastError();
 }
 
