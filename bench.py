@@ -149,7 +149,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     import paper_1411_5283_gb300 as bs
-    from paper_1411_5283_gb300 import synth
+    from paper_1411_5283_gb300 import replicas, synth
 
     bs._lib.load()
     dev = torch.device("cuda", local_rank)
@@ -204,11 +204,7 @@ def run_ours(args, rank, world, local_rank):
     bs.bsort_profile_enable(False)
     prof = bs.bsort_profile_read()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
 
     # ---- end to end through the C ABI with host buffers -------------------
     out_rec_h = torch.empty((n, W), dtype=torch.uint8).pin_memory()
@@ -233,11 +229,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / k2
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / k2, dev)
 
     # ---- roofline of the dominant kernel ----------------------------------
     off = s.off.cpu().numpy().view(np.uint32).astype(np.int64)
@@ -486,9 +478,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     r = run_ours(args, rank, world, local_rank)
     if r is not None and rank == 0:
+        from paper_1411_5283_gb300 import replicas
         n_total = r["n"] * world
-        value = n_total / (r["ms"] * 1e-3) / 1e6
-        e2e_value = n_total / (r["e2e_ms"] * 1e-3) / 1e6
+        value = replicas.throughput(n_total, r["ms"])
+        e2e_value = replicas.throughput(n_total, r["e2e_ms"])
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "Mwords/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
