@@ -813,12 +813,14 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 
 // Exclusive prefix sums of the per-warp digit counts hist[w][d] in (digit,
 // warp) order, written back in place: afterwards hist[w][d] is the first
-// output position of warp w's items with digit d.  Thread t scans digit t/2
-// for warps 8(t%2) .. 8(t%2)+7, so thread order is (digit, warp) order.
+// output position of warp w's items with digit d.  Thread t scans the eight
+// entries 8t .. 8t+7 of that order (entry e = digit e / warps, warp
+// e % warps), so thread order is (digit, warp) order.
 __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp_tmp) {
   static_assert(kSegThreads * 8 == kRxWarps * kRxDigits, "eight counters per thread");
+  static_assert(kRxWarps % 8 == 0, "a thread's eight entries share one digit");
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
-  uint16_t* h = hist + ((t & 1u) * 8) * kRxDigits + (t >> 1);  // entry (warp 8(t%2) + k, digit t/2)
+  uint16_t* h = hist + ((8 * t) % kRxWarps) * kRxDigits + (8 * t) / kRxWarps;  // entry (warp, digit) of 8t
   uint32_t v[8], sum = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -852,12 +854,15 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
                                                  St st, uint16_t* hist, uint32_t* warp_tmp) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t S = ((c + kRxWarps - 1) / kRxWarps + 31) & ~31u;
-  const uint32_t w0 = warp * S, lt = lanemask_lt();
+  const uint32_t w0 = warp * S, p0 = w0 + lane, lt = lanemask_lt();
+  // item j is in the warp's range when j < nr (warp-uniform) and holds a
+  // position below c as well when j < nv (<= nr)
+  const uint32_t nr = S / 32, nv = min(nr, c > p0 ? (c - p0 + 31) / 32 : 0u);
   uint16_t* row = hist + warp * kRxDigits;
   It x[E];
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (static_cast<uint32_t>(j) * 32 < S && w0 + j * 32 + lane < c) x[j] = get(w0 + j * 32 + lane);
+    if (j < nv) x[j] = get(p0 + 32 * j);
   // every item is read before the first pass scatters into the store
   __syncthreads();
   uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
@@ -866,8 +871,8 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      if (static_cast<uint32_t>(j) * 32 < S) {  // warp-uniform
-        const bool valid = w0 + j * 32 + lane < c;
+      if (j < nr) {  // warp-uniform
+        const bool valid = j < nv;
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
         const uint32_t d = x[j].digit(s, ib);
         const uint32_t peers = digit_peers(d) & vm;
@@ -888,7 +893,7 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
     scan_digit_counts(hist, warp_tmp);
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      if (static_cast<uint32_t>(j) * 32 < S && w0 + j * 32 + lane < c) {
+      if (j < nv) {
         const uint32_t r = (j & 1) ? rk[j / 2] >> 16 : rk[j / 2] & 0xffffu;
         st.store(row[x[j].digit(s, ib)] + r, x[j]);
       }
@@ -897,7 +902,7 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
     if (s + 8 < bits) {
 #pragma unroll
       for (int j = 0; j < E; ++j)
-        if (static_cast<uint32_t>(j) * 32 < S && w0 + j * 32 + lane < c) x[j] = st.load(w0 + j * 32 + lane);
+        if (j < nv) x[j] = st.load(p0 + 32 * j);
     }
   }
 }
@@ -1224,17 +1229,24 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_hist", auto_hist_kernel, static_cast<uint32_t>(g_sm_count) * 4, kHistThreads,
                0, s, len, n_cap, d_n, W, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_offsets", auto_offsets_kernel, 1, 64, 0, s, W, ws, v, d_off);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_sample", auto_sample_kernel, (samples + 255) / 256, 256, 0, s, rec, len,
                n_cap, d_n, W, d_off, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, s,
                d_off, W, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_select", auto_spl_select_kernel, dim3(W, kSplChunks), 1024, 0, s, d_off, W,
                ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, W, 288, 0, s, d_off, W, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = partition(rec, len, n_cap, d_n, W, d_off, ws, v, 0, s);
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_layout", auto_layout_kernel, 1, 1024, 0, s, W, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = partition(rec, len, n_cap, d_n, W, d_off, ws, v, 1, s);
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_segsort", auto_segsort_kernel, static_cast<uint32_t>(g_sm_count) * 2,

@@ -171,7 +171,8 @@ inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
 // `current` remembers the limit already set for that kernel.
 template <typename Kernel>
 inline cudaError_t ensure_smem(Kernel k, size_t bytes, size_t* current) {
-  if (bytes <= 48 * 1024 || bytes <= *current) return cudaSuccess;
+  // always opt in: static shared memory counts against the 48 KB default too
+  if (bytes <= *current) return cudaSuccess;
   const cudaError_t e =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e == cudaSuccess) *current = bytes;
