@@ -208,30 +208,46 @@ auto_sample_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
                    const uint32_t* __restrict__ d_off, Ws ws, AutoView av) {
   __shared__ BucketPlan plans[kMaxW + 1];
   __shared__ uint32_t s_off[kMaxW + 2];
+  __shared__ uint32_t thr[kMaxW + 1], bcnt[kMaxW + 1], bbase[kMaxW + 1];
   const AutoView& v = av;
   load_plans(plans, s_off, d_off, W, v.cap);
+  // Acceptance probability per bucket: about 20 samples per expected segment
+  // (segments expect 2730 / 1365 / 682 words for 1 / 2 / >= 3 keys, positions
+  // are one per 32 words), but never more than 90 % of the bucket's sample
+  // capacity.  The capacity must not truncate: the index is part of the sort
+  // key, so a truncated sample would miss the later copies of a frequent word.
+  // A position is kept when the high word of its hash is below thr[L].
+  if (threadIdx.x <= W) {
+    const uint32_t L = threadIdx.x;
+    const BucketPlan& p = plans[L];
+    uint32_t t = 0;
+    if (L >= 1 && p.g >= 2) {
+      const uint32_t cnt = s_off[L + 1] - s_off[L];
+      const double want = p.K == 1 ? 0.25 : (p.K == 2 ? 0.5 : 1.0);
+      const double room = 0.9 * p.scap * static_cast<double>(kAutoSampleEvery) / cnt;
+      const double q = want < room ? want : room;
+      t = q >= 1.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(q * 4294967296.0);
+    }
+    thr[L] = t;
+    bcnt[L] = 0;
+  }
+  __syncthreads();
   const uint32_t n = word_count(n_cap, d_n);
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t h = mix64(s + 0x9E3779B97F4A7C15ull);
   const uint64_t i64 = static_cast<uint64_t>(s) * kAutoSampleEvery + (h & (kAutoSampleEvery - 1));
-  if (i64 >= n) return;
   const uint32_t i = static_cast<uint32_t>(i64);
-  const uint32_t L = len[i];
-  if (L == 0 || L > W) return;
+  uint32_t L = i64 < n ? len[i] : 0u;
+  if (L > W || static_cast<uint32_t>(h >> 32) >= thr[L]) L = 0;  // thr[0] = 0: never kept
+  // slots: counted per bucket in the block, one global reservation per bucket
+  const uint32_t local = L ? atomicAdd(&bcnt[L], 1u) : 0u;
+  __syncthreads();
+  if (threadIdx.x <= W && bcnt[threadIdx.x])
+    bbase[threadIdx.x] = atomicAdd(&v.hdr->samp_cnt[threadIdx.x], bcnt[threadIdx.x]);
+  __syncthreads();
+  if (!L) return;
   const BucketPlan& p = plans[L];
-  if (p.g < 2) return;  // one segment: no splitters needed
-  // Acceptance probability: about 20 samples per expected segment (segments
-  // expect 2730 / 1365 / 682 words for 1 / 2 / >= 3 keys, positions are one per
-  // 32 words), but never more than 90 % of the bucket's sample capacity.  The
-  // capacity must not truncate: arrivals come in position order, and the input
-  // index is part of the sort key, so a truncated sample would cover only the
-  // early copies of a frequent word.
-  const uint32_t cnt = s_off[L + 1] - s_off[L];
-  const double want = p.K == 1 ? 0.25 : (p.K == 2 ? 0.5 : 1.0);
-  const double room = 0.9 * p.scap * static_cast<double>(kAutoSampleEvery) / cnt;
-  const double q = want < room ? want : room;
-  if (static_cast<double>(h >> 32) >= q * 4294967296.0) return;
-  const uint32_t slot = atomicAdd(&v.hdr->samp_cnt[L], 1u);
+  const uint32_t slot = bbase[L] + local;
   if (slot >= p.scap) return;
   const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
   for (uint32_t k = 0; k < p.K; ++k)
@@ -326,8 +342,16 @@ auto_spl_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, Auto
   }
 }
 
+// (b) ranks.  The CTA stages the bucket's sorted first key words and indices
+// in shared memory (kSplSelectSmem); a tie on the first word with more key
+// words reads the rest from the sample planes.
+constexpr size_t kSplSelectSmem = static_cast<size_t>(auto_sample_max(1)) * 12;
+static_assert(auto_sample_max(2) * 12 <= kSplSelectSmem && auto_sample_max(3) * 12 <= kSplSelectSmem,
+              "every bucket's first key words and indices fit the staging area");
+
 template <int K>
-__device__ void select_splitters(const AutoView& v, const BucketPlan& p, uint32_t m, uint32_t j) {
+__device__ void select_splitters(uint8_t* smem, const AutoView& v, const BucketPlan& p, uint32_t m,
+                                 uint32_t j) {
   constexpr uint32_t CH = spl_chunk(K);
   const uint32_t ns = p.g - 1;
   uint64_t* sk = reinterpret_cast<uint64_t*>(v.spl + p.spl_off + kDirBytes);
@@ -347,8 +371,26 @@ __device__ void select_splitters(const AutoView& v, const BucketPlan& p, uint32_
   const uint32_t cnt = min(CH, m - lo);
   const uint32_t chunks = (m + CH - 1) / CH;
   const SmemTile<K> g = sample_tile<K>(v, p);
+  uint64_t* k0s = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* ids = reinterpret_cast<uint32_t*>(k0s + m);
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+    k0s[i] = g.k[0][i];
+    ids[i] = g.idx[i];
+  }
+  __syncthreads();
+  // is sample q (sorted position) below element e (at sorted position x)?
+  auto below = [&](uint32_t q, const Elem<K>& e) {
+    const uint64_t a = k0s[q];
+    if (a != e.k[0]) return a < e.k[0];
+    if constexpr (K == 1) return ids[q] < e.idx;
+    else return elem_less<K>(g.get(q), e);
+  };
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const Elem<K> e = g.get(lo + i);
+    Elem<K> e;
+    e.k[0] = k0s[lo + i];
+#pragma unroll
+    for (int k = 1; k < K; ++k) e.k[k] = g.k[k][lo + i];
+    e.idx = ids[lo + i];
     // binary searches in all other chunks in lockstep (independent loads)
     uint32_t a[kSplChunks], b[kSplChunks];
 #pragma unroll
@@ -361,7 +403,7 @@ __device__ void select_splitters(const AutoView& v, const BucketPlan& p, uint32_
       for (uint32_t q = 0; q < kSplChunks; ++q) {
         if (a[q] < b[q]) {
           const uint32_t mid = (a[q] + b[q]) >> 1;
-          if (elem_less<K>(g.get(q * CH + mid), e)) a[q] = mid + 1;
+          if (below(q * CH + mid, e)) a[q] = mid + 1;
           else b[q] = mid;
         }
       }
@@ -385,6 +427,7 @@ __device__ void select_splitters(const AutoView& v, const BucketPlan& p, uint32_
 // bucket L and writes those that are splitters.
 __global__ void __launch_bounds__(1024)
 auto_spl_select_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
+  extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ BucketPlan p;
   const AutoView& v = av;
@@ -396,10 +439,10 @@ auto_spl_select_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, Au
   if (p.g < 2) return;
   const uint32_t m = min(v.hdr->samp_cnt[L], p.scap);
   switch (p.K) {
-    case 1: select_splitters<1>(v, p, m, j); break;
-    case 2: select_splitters<2>(v, p, m, j); break;
-    case 3: select_splitters<3>(v, p, m, j); break;
-    default: select_splitters<4>(v, p, m, j); break;
+    case 1: select_splitters<1>(smem, v, p, m, j); break;
+    case 2: select_splitters<2>(smem, v, p, m, j); break;
+    case 3: select_splitters<3>(smem, v, p, m, j); break;
+    default: select_splitters<4>(smem, v, p, m, j); break;
   }
 }
 
@@ -1211,8 +1254,9 @@ bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W) {
 cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
                         uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {
-  static size_t split_set = 0, seg_set = 0;
+  static size_t split_set = 0, select_set = 0, seg_set = 0;
   cudaError_t e = ensure_smem(auto_spl_sort_kernel, kSplSortSmem, &split_set);
+  if (e == cudaSuccess) e = ensure_smem(auto_spl_select_kernel, kSplSelectSmem, &select_set);
   if (e == cudaSuccess) e = ensure_smem(auto_segsort_kernel, segsort_smem_bytes(), &seg_set);
   if (e != cudaSuccess) return e;
   if (g_sm_count == 0) {
@@ -1238,8 +1282,8 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, s,
                d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_spl_select", auto_spl_select_kernel, dim3(W, kSplChunks), 1024, 0, s, d_off, W,
-               ws, v);
+  BSORT_LAUNCH("auto_spl_select", auto_spl_select_kernel, dim3(W, kSplChunks), 1024, kSplSelectSmem,
+               s, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, W, 288, 0, s, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
