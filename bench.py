@@ -33,9 +33,33 @@ N_WORDS = 16_777_216
 W = 32
 SEED = 2
 
-# dram bytes per launch from the committed ncu summaries (profiles/), by kernel;
-# None where no capture of the current kernel exists yet.
-NCU_TRAFFIC = {}
+# DRAM bytes per full-size launch from the committed ncu summaries (profiles/),
+# by kernel, with the SHA-1 prefix of the kernel sources they were taken on:
+# reported only while the sources still match (else null).
+NCU_TRAFFIC = {
+    # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
+    # cut of the table (65.61 + 108.03 MB), x4 for 16,777,216 words; a lower
+    # bound: at 4M words part of the partition output is still in L2
+    "auto_segsort": {"bytes": 4 * (65.61e6 + 108.03e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8a3e97dffb76",
+                                 "paper_1411_5283_gb300/csrc/common.cuh": "03f6103478f2"}},
+    "auto_partition": {"bytes": 4 * (139.0e6 + 28.06e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8a3e97dffb76",
+                                   "paper_1411_5283_gb300/csrc/common.cuh": "03f6103478f2"}},
+}
+
+
+def ncu_traffic(kernel: str):
+    """Committed DRAM traffic of kernel's launch, or None when its sources changed."""
+    import hashlib
+    e = NCU_TRAFFIC.get(kernel)
+    if not e:
+        return None
+    for path, want in e["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest()[:len(want)] != want:
+                return None
+    return round(e["bytes"])
 
 
 def parse():
@@ -250,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
         "ms": ms, "e2e_ms": e2e_ms, "n": n, "prof": prof, "clk": clk,
         "roofline": {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": NCU_TRAFFIC.get(name), "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(name), "peak_kind": peak_kind,
                      "launches_per_step": launches / steps_prof,
                      "algorithmic_bytes_per_step": bytes_step},
         "path_roofline": {"compulsory_bytes_per_word": W + 1 + W + 4,
