@@ -692,13 +692,14 @@ auto_layout_kernel(uint32_t W, Ws ws, AutoView av) {
 // warp) and warp totals follow its planes.
 constexpr uint32_t kRxWarps = kSegThreads / 32;
 constexpr uint32_t kRxDigits = 256;
-constexpr size_t kRxHistBytes = kRxWarps * kRxDigits * sizeof(uint16_t) + kRxWarps * sizeof(uint32_t);
+constexpr size_t kRxHistBytes =
+    kRxWarps * kRxDigits * sizeof(uint16_t) + 2 * kRxWarps * sizeof(uint32_t);  // counters, warp sums + maxima
 
 __host__ __device__ constexpr size_t seg_plane_elems(uint32_t K) { return auto_seg_cap(K); }
 
 // >= max over K of the planes (8K + 4 bytes per element), and the one-key
 // planes plus the radix counters (checked below)
-constexpr size_t kSegPlanesBytes = 106560;
+constexpr size_t kSegPlanesBytes = 106624;
 
 // One segment buffer per CTA (two CTAs per SM overlap each other's copies,
 // sorts and stores): barrier + planes.
@@ -885,6 +886,85 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
   __syncthreads();
 }
 
+// Bucket pass for one-word items: the items (distinct integers below 2^bits)
+// are counted by their top kMsdBits bits in 2^kMsdBits shared counters,
+// scattered to their bucket's range, and every bucket is then sorted by one
+// thread (insertion sort).  Used when no bucket holds more than
+// kMsdMaxBucket items, which is the usual case: a segment's items spread over
+// their range because the index part is spread over the input.  Returns false,
+// with the items untouched in registers, when the counts are too uneven (then
+// the radix passes run).  cnt holds 2^kMsdBits words.
+constexpr uint32_t kMsdBits = 13;
+constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
+constexpr uint32_t kMsdMaxBucket = 32;
+constexpr uint32_t kMsdKeyBits = 10;
+
+template <int E>
+__device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t nr, uint32_t nv,
+                                                  uint32_t p0, uint32_t bits, uint64_t* a,
+                                                  uint32_t* cnt, uint32_t* warp_tmp) {
+  (void)nr;
+  (void)p0;
+  const uint32_t sh = bits > kMsdBits ? bits - kMsdBits : 0u;
+  constexpr uint32_t per = kMsdBuckets / kSegThreads;  // counters per thread
+  static_assert(per * kSegThreads == kMsdBuckets, "counters split evenly over the threads");
+  uint32_t* mine = cnt + threadIdx.x * per;
+#pragma unroll
+  for (uint32_t k = 0; k < per; ++k) mine[k] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (j < nv) atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u);
+  __syncthreads();
+  // exclusive scan of the counts (thread t owns counters t*per .. t*per+per-1)
+  uint32_t v[per], sum = 0, mx = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < per; ++k) {
+    v[k] = mine[k];
+    sum += v[k];
+    mx = v[k] > mx ? v[k] : mx;
+  }
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t inc = warp_inclusive_scan(sum);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 31) warp_tmp[warp] = inc;
+  if (lane == 0) warp_tmp[kRxWarps + warp] = mx;
+  __syncthreads();
+  const uint32_t tw = lane < kRxWarps ? warp_tmp[lane] : 0u;
+  const uint32_t tupto = warp_inclusive_scan(tw);
+  uint32_t tm = lane < kRxWarps ? warp_tmp[kRxWarps + lane] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tm = max(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+  if (tm > kMsdMaxBucket) return false;  // block-uniform
+  uint32_t run = __shfl_sync(0xffffffffu, tupto - tw, warp) + inc - sum;
+#pragma unroll
+  for (uint32_t k = 0; k < per; ++k) {
+    mine[k] = run;  // bucket start, then its cursor
+    run += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (j < nv) a[atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u)] = x[j].v;
+  __syncthreads();
+  // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b))
+  for (uint32_t b = threadIdx.x; b < kMsdBuckets; b += kSegThreads) {
+    const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
+    for (uint32_t i = lo + 1; i < hi; ++i) {
+      const uint64_t key = a[i];
+      uint32_t q = i;
+      while (q > lo && a[q - 1] > key) {
+        a[q] = a[q - 1];
+        --q;
+      }
+      a[q] = key;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // Stable LSD radix sort of c items, held in registers: warp w owns positions
 // [w S, w S + S) (S = ceil(c / warps) rounded up to 32), lane l holds
 // position w S + 32 j + l in x[j], read through get(p).  Each pass ranks the
@@ -894,7 +974,8 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 // end in st[0, c).
 template <typename It, typename St, int E, typename Get>
 __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t bits, uint32_t ib,
-                                                 St st, uint16_t* hist, uint32_t* warp_tmp) {
+                                                 St st, uint16_t* hist, uint32_t* warp_tmp,
+                                                 uint32_t* bucket_cnt) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t S = ((c + kRxWarps - 1) / kRxWarps + 31) & ~31u;
   const uint32_t w0 = warp * S, p0 = w0 + lane, lt = lanemask_lt();
@@ -908,6 +989,14 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
     if (j < nv) x[j] = get(p0 + 32 * j);
   // every item is read before the first pass scatters into the store
   __syncthreads();
+  // the bucket pass needs evenly spread top bits: key bytes use few of their
+  // 256 values, so it is tried only when the key part is at most kMsdKeyBits
+  // wide and index bits fill the rest of the window
+  if constexpr (sizeof(It) == sizeof(Item64)) {
+    if (bucket_cnt && bits > 8 && bits - ib <= kMsdKeyBits &&
+        bucket_sort_items<E>(x, nr, nv, p0, bits, st.a, bucket_cnt, warp_tmp))
+      return;
+  }
   uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
   for (uint32_t s = 0; s < bits; s += 8) {
     for (uint32_t i = lane; i < kRxDigits; i += 32) row[i] = 0;
@@ -967,7 +1056,8 @@ __device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, uint32_t shi
   uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
   if constexpr (sizeof(It) == sizeof(Item64)) {
     auto get = [=](uint32_t p) { return Item64{(((kp[p] >> shift) - k0) << ib) | ip[p]}; };
-    radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp);
+    // the index plane is free once the items are in registers: bucket counters
+    radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp, ip);
     const uint64_t imask = (1ull << ib) - 1;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       const uint64_t v = kp[r];
@@ -978,7 +1068,7 @@ __device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, uint32_t shi
     }
   } else {
     auto get = [=](uint32_t p) { return Item96{(kp[p] >> shift) - k0, ip[p]}; };
-    radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp);
+    radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp, nullptr);
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       Elem<1> e;
       e.k[0] = (kp[r] + k0) << shift;
@@ -1224,6 +1314,7 @@ static_assert(16 * kSegThreads >= auto_seg_cap(1), "16 radix items per thread co
 static_assert(auto_seg_cap(1) * 12 + kRxHistBytes <= kSegPlanesBytes,
               "one-key planes and radix counters exceed the segment buffer");
 static_assert(3 * kRxWarps * 8 <= kRxHistBytes, "reduction scratch fits the radix counters");
+static_assert(kMsdBuckets <= auto_seg_cap(1), "bucket counters fit the index plane");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
 // a few scalars; ptxas -v reports it) + 1 KB reserved each
 static_assert(2 * (segsort_smem_bytes() + 256 + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");
