@@ -806,6 +806,37 @@ __device__ bool maybe_prefetch(uint8_t* buf, const AutoView& v, uint32_t seg, ui
   return true;
 }
 
+// ---- one-key segments: byte recoding -----------------------------------
+// A one-key segment's keys (big-endian, bytes past the word zero) are recoded
+// position by position: byte position p (0 = most significant) maps value b to
+// b - lo_p in a field as wide as hi_p - lo_p needs, where lo_p and hi_p are
+// the smallest and largest byte at p in the segment, and the fields are laid
+// out most significant first.  The code orders like the key (the byte order is
+// kept within every field and the fields follow the byte positions) and
+// decodes back exactly.  Positions where all words agree take no bits, and a
+// position of letters takes 5, so codes are narrow and their top bits spread.
+struct ByteCode {
+  uint32_t f[8];  // position p: lo_p | offset_p << 8 | width_p << 16
+  __device__ __forceinline__ uint64_t encode(uint64_t key) const {
+    uint64_t code = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const uint32_t b = static_cast<uint32_t>(key >> (56 - 8 * p)) & 255u;
+      code |= static_cast<uint64_t>(b - (f[p] & 255u)) << ((f[p] >> 8) & 63u);
+    }
+    return code;
+  }
+  __device__ __forceinline__ uint64_t decode(uint64_t code) const {
+    uint64_t key = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const uint32_t b = static_cast<uint32_t>(code >> ((f[p] >> 8) & 63u)) & ((1u << (f[p] >> 16)) - 1u);
+      key |= static_cast<uint64_t>(b + (f[p] & 255u)) << (56 - 8 * p);
+    }
+    return key;
+  }
+};
+
 // ---- one-key segments: LSD radix sort -----------------------------------
 // A one-key segment (words of at most 8 letters) orders its elements by the
 // integer (key - kmin) * 2^ib + idx, where key is the word's key without its
@@ -897,7 +928,6 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
 constexpr uint32_t kMsdMaxBucket = 32;
-constexpr uint32_t kMsdKeyBits = 10;
 
 template <int E>
 __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t nr, uint32_t nv,
@@ -989,11 +1019,9 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
     if (j < nv) x[j] = get(p0 + 32 * j);
   // every item is read before the first pass scatters into the store
   __syncthreads();
-  // the bucket pass needs evenly spread top bits: key bytes use few of their
-  // 256 values, so it is tried only when the key part is at most kMsdKeyBits
-  // wide and index bits fill the rest of the window
+  // byte-recoded keys spread their top bits: the bucket pass is tried first
   if constexpr (sizeof(It) == sizeof(Item64)) {
-    if (bucket_cnt && bits > 8 && bits - ib <= kMsdKeyBits &&
+    if (bucket_cnt && bits > 8 &&
         bucket_sort_items<E>(x, nr, nv, p0, bits, st.a, bucket_cnt, warp_tmp))
       return;
   }
@@ -1045,9 +1073,9 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
 // compiles to a shared-memory instruction.  Not inlined: the caller's segment
 // loop keeps its own state live, and the items need the registers.
 template <typename It, int E>
-__device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, uint32_t shift, uint64_t k0,
-                                      uint32_t kb, uint32_t ib, uint32_t W, uint32_t ob,
-                                      uint8_t* out_rec, uint32_t* out_perm) {
+__device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, ByteCode bc, uint32_t kb,
+                                      uint32_t ib, uint32_t W, uint32_t ob, uint8_t* out_rec,
+                                      uint32_t* out_perm) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   constexpr uint32_t C = auto_seg_cap(1);
   uint64_t* kp = reinterpret_cast<uint64_t*>(smem_raw + buf_off);
@@ -1055,45 +1083,28 @@ __device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, uint32_t shi
   uint16_t* hist = reinterpret_cast<uint16_t*>(ip + C);
   uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
   if constexpr (sizeof(It) == sizeof(Item64)) {
-    auto get = [=](uint32_t p) { return Item64{(((kp[p] >> shift) - k0) << ib) | ip[p]}; };
+    auto get = [=](uint32_t p) { return Item64{(bc.encode(kp[p]) << ib) | ip[p]}; };
     // the index plane is free once the items are in registers: bucket counters
     radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp, ip);
     const uint64_t imask = (1ull << ib) - 1;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       const uint64_t v = kp[r];
       Elem<1> e;
-      e.k[0] = ((v >> ib) + k0) << shift;
+      e.k[0] = bc.decode(v >> ib);
       e.idx = static_cast<uint32_t>(v & imask);
       write_word<1>(W, out_rec, out_perm, ob + r, e);
     }
   } else {
-    auto get = [=](uint32_t p) { return Item96{(kp[p] >> shift) - k0, ip[p]}; };
+    auto get = [=](uint32_t p) { return Item96{bc.encode(kp[p]), ip[p]}; };
     radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp, nullptr);
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       Elem<1> e;
-      e.k[0] = (kp[r] + k0) << shift;
+      e.k[0] = bc.decode(kp[r]);
       e.idx = ip[r];
       write_word<1>(W, out_rec, out_perm, ob + r, e);
     }
   }
   __syncthreads();
-}
-
-__device__ __forceinline__ uint64_t warp_min64(uint64_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
-    x = y < x ? y : x;
-  }
-  return x;
-}
-__device__ __forceinline__ uint64_t warp_max64(uint64_t x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
-    x = y > x ? y : x;
-  }
-  return x;
 }
 
 // Segments of words with two or more key words (longer than 8 letters, a
@@ -1115,60 +1126,81 @@ __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uin
   __syncthreads();
 }
 
-// One-key segment of length-L words resident in buf: find kmin, kmax and the
-// largest index, then radix-sort the (key - kmin, index) items.
+// One-key segment resident in buf: byte-wise minima and maxima of its keys
+// and the largest index give the byte code and the index width, then the
+// (code, index) items are sorted.
 __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
-                                 uint32_t seg, uint32_t c, uint32_t L, uint32_t W, uint8_t* out_rec,
+                                 uint32_t seg, uint32_t c, uint32_t W, uint8_t* out_rec,
                                  uint32_t* out_perm) {
-  __shared__ uint64_t s_kmin;
-  __shared__ uint32_t s_kb, s_ib;
+  __shared__ uint32_t s_f[8], s_kb, s_ib;
   constexpr uint32_t C = auto_seg_cap(1);
   uint64_t* kp = reinterpret_cast<uint64_t*>(buf + 16);
   uint32_t* ip = reinterpret_cast<uint32_t*>(kp + C);
   // per-warp partial results in the (not yet used) radix counter area
-  uint64_t (*red)[kSegThreads / 32] = reinterpret_cast<uint64_t (*)[kSegThreads / 32]>(ip + C);
-  const uint32_t shift = 64 - 8 * L;  // L <= 8: the low 64-8L key bits are zero
-  uint64_t kmin = ~0ull, kmax = 0, imax = 0;
+  uint32_t (*red)[kSegThreads / 32] = reinterpret_cast<uint32_t (*)[kSegThreads / 32]>(ip + C);
+  uint32_t lo_h = ~0u, lo_l = ~0u, hi_h = 0, hi_l = 0, imax = 0;
   for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
-    const uint64_t k = kp[i] >> shift;
-    kmin = k < kmin ? k : kmin;
-    kmax = k > kmax ? k : kmax;
-    imax = ip[i] > imax ? ip[i] : imax;
+    const uint64_t k = kp[i];
+    const uint32_t h = static_cast<uint32_t>(k >> 32), l = static_cast<uint32_t>(k);
+    lo_h = __vminu4(lo_h, h);
+    lo_l = __vminu4(lo_l, l);
+    hi_h = __vmaxu4(hi_h, h);
+    hi_l = __vmaxu4(hi_l, l);
+    imax = max(imax, ip[i]);
   }
-  kmin = warp_min64(kmin);
-  kmax = warp_max64(kmax);
-  imax = warp_max64(imax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo_h = __vminu4(lo_h, __shfl_xor_sync(0xffffffffu, lo_h, o));
+    lo_l = __vminu4(lo_l, __shfl_xor_sync(0xffffffffu, lo_l, o));
+    hi_h = __vmaxu4(hi_h, __shfl_xor_sync(0xffffffffu, hi_h, o));
+    hi_l = __vmaxu4(hi_l, __shfl_xor_sync(0xffffffffu, hi_l, o));
+    imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+  }
   const uint32_t warp = threadIdx.x >> 5;
   if (lane_id() == 0) {
-    red[0][warp] = kmin;
-    red[1][warp] = kmax;
-    red[2][warp] = imax;
+    red[0][warp] = lo_h;
+    red[1][warp] = lo_l;
+    red[2][warp] = hi_h;
+    red[3][warp] = hi_l;
+    red[4][warp] = imax;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint64_t a = ~0ull, b = 0, m = 0;
+    uint32_t a = ~0u, b = ~0u, x = 0, y = 0, m = 0;
     for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-      a = red[0][w] < a ? red[0][w] : a;
-      b = red[1][w] > b ? red[1][w] : b;
-      m = red[2][w] > m ? red[2][w] : m;
+      a = __vminu4(a, red[0][w]);
+      b = __vminu4(b, red[1][w]);
+      x = __vmaxu4(x, red[2][w]);
+      y = __vmaxu4(y, red[3][w]);
+      m = max(m, red[4][w]);
     }
-    s_kmin = a;
-    s_kb = b == a ? 0u : 64u - static_cast<uint32_t>(__clzll(b - a));
-    s_ib = 32u - static_cast<uint32_t>(__clz(static_cast<uint32_t>(m) | 1u));
+    const uint64_t lo = (static_cast<uint64_t>(a) << 32) | b, hi = (static_cast<uint64_t>(x) << 32) | y;
+    uint32_t off = 0;
+    for (int p = 7; p >= 0; --p) {
+      const uint32_t l = static_cast<uint32_t>(lo >> (56 - 8 * p)) & 255u;
+      const uint32_t h = static_cast<uint32_t>(hi >> (56 - 8 * p)) & 255u;
+      const uint32_t wdt = h > l ? 32u - static_cast<uint32_t>(__clz(h - l)) : 0u;
+      s_f[p] = l | (off << 8) | (wdt << 16);
+      off += wdt;
+    }
+    s_kb = off;
+    s_ib = 32u - static_cast<uint32_t>(__clz(m | 1u));
   }
   __syncthreads();
+  ByteCode bc;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) bc.f[p] = s_f[p];
   const uint32_t kb = s_kb, ib = s_ib;
-  const uint64_t k0 = s_kmin;
   const uint32_t ob = v.outbase[seg];
   const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);
   if (kb + ib <= 64) {
-    if (c <= 4 * kSegThreads) k1_radix<Item64, 4>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
-    else if (c <= 8 * kSegThreads) k1_radix<Item64, 8>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
-    else k1_radix<Item64, 16>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
+    if (c <= 4 * kSegThreads) k1_radix<Item64, 4>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
+    else if (c <= 8 * kSegThreads) k1_radix<Item64, 8>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
+    else k1_radix<Item64, 16>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
   } else {
-    if (c <= 4 * kSegThreads) k1_radix<Item96, 4>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
-    else if (c <= 8 * kSegThreads) k1_radix<Item96, 8>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
-    else k1_radix<Item96, 16>(off, c, shift, k0, kb, ib, W, ob, out_rec, out_perm);
+    if (c <= 4 * kSegThreads) k1_radix<Item96, 4>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
+    else if (c <= 8 * kSegThreads) k1_radix<Item96, 8>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
+    else k1_radix<Item96, 16>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
   }
 }
 
@@ -1219,7 +1251,7 @@ auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_re
       return;
     }
     switch (K) {
-      case 1: sort_resident_k1(smem_raw, buf, v, seg, c, L, W, out_rec, out_perm); break;
+      case 1: sort_resident_k1(smem_raw, buf, v, seg, c, W, out_rec, out_perm); break;
       case 2: sort_resident<2>(buf, v, seg, c, W, out_rec, out_perm); break;
       case 3: sort_resident<3>(buf, v, seg, c, W, out_rec, out_perm); break;
       default: sort_resident<4>(buf, v, seg, c, W, out_rec, out_perm); break;
@@ -1313,7 +1345,7 @@ static_assert(seg_plane_elems(1) * 12 <= kSegPlanesBytes && seg_plane_elems(2) *
 static_assert(16 * kSegThreads >= auto_seg_cap(1), "16 radix items per thread cover a one-key segment");
 static_assert(auto_seg_cap(1) * 12 + kRxHistBytes <= kSegPlanesBytes,
               "one-key planes and radix counters exceed the segment buffer");
-static_assert(3 * kRxWarps * 8 <= kRxHistBytes, "reduction scratch fits the radix counters");
+static_assert(5 * kRxWarps * 4 <= kRxHistBytes, "reduction scratch fits the radix counters");
 static_assert(kMsdBuckets <= auto_seg_cap(1), "bucket counters fit the index plane");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
 // a few scalars; ptxas -v reports it) + 1 KB reserved each
