@@ -1126,6 +1126,146 @@ __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uin
   __syncthreads();
 }
 
+// Two-key segments (words of 9 to 16 letters) whose byte code fits 64 bits:
+// the same item sort on the code of all 16 byte positions.  The code table
+// (16 fields, as in ByteCode) is read from shared memory at f.  Key planes 0
+// and 1 and the index plane hold the segment; plane 0 becomes the item store
+// and plane 1 the bucket counters.
+__device__ __forceinline__ uint64_t encode16(const uint32_t* f, uint64_t k0, uint64_t k1) {
+  uint64_t code = 0;
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    const uint64_t k = p < 8 ? k0 : k1;
+    const uint32_t b = static_cast<uint32_t>(k >> (56 - 8 * (p & 7))) & 255u;
+    code |= static_cast<uint64_t>(b - (f[p] & 255u)) << ((f[p] >> 8) & 63u);
+  }
+  return code;
+}
+__device__ __forceinline__ void decode16(const uint32_t* f, uint64_t code, Elem<2>& e) {
+  e.k[0] = 0;
+  e.k[1] = 0;
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    const uint32_t b = static_cast<uint32_t>(code >> ((f[p] >> 8) & 63u)) & ((1u << (f[p] >> 16)) - 1u);
+    e.k[p >> 3] |= static_cast<uint64_t>(b + (f[p] & 255u)) << (56 - 8 * (p & 7));
+  }
+}
+
+template <typename It, int E>
+__device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32_t* f, uint32_t kb,
+                                      uint32_t ib, uint32_t W, uint32_t ob, uint8_t* out_rec,
+                                      uint32_t* out_perm) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  constexpr uint32_t C = auto_seg_cap(2);
+  static_assert(2 * C >= kMsdBuckets, "plane 1 holds the bucket counters");
+  uint64_t* k0p = reinterpret_cast<uint64_t*>(smem_raw + buf_off);
+  uint64_t* k1p = k0p + C;
+  uint32_t* ip = reinterpret_cast<uint32_t*>(k1p + C);
+  uint16_t* hist = reinterpret_cast<uint16_t*>(ip + C);
+  uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
+  if constexpr (sizeof(It) == sizeof(Item64)) {
+    auto get = [=](uint32_t p) { return Item64{(encode16(f, k0p[p], k1p[p]) << ib) | ip[p]}; };
+    radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{k0p}, hist, warp_tmp,
+                                     reinterpret_cast<uint32_t*>(k1p));
+    const uint64_t imask = (1ull << ib) - 1;
+    for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
+      const uint64_t v = k0p[r];
+      Elem<2> e;
+      decode16(f, v >> ib, e);
+      e.idx = static_cast<uint32_t>(v & imask);
+      write_word<2>(W, out_rec, out_perm, ob + r, e);
+    }
+  } else {
+    auto get = [=](uint32_t p) { return Item96{encode16(f, k0p[p], k1p[p]), ip[p]}; };
+    radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{k0p, ip}, hist, warp_tmp, nullptr);
+    for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
+      Elem<2> e;
+      decode16(f, k0p[r], e);
+      e.idx = ip[r];
+      write_word<2>(W, out_rec, out_perm, ob + r, e);
+    }
+  }
+  __syncthreads();
+}
+
+// Two-key segment resident in buf: byte-wise minima and maxima over the 16 key
+// bytes; a code of at most 64 bits takes the item sort, a wider one the
+// bitonic network.  Returns false when the code is too wide.
+__device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
+                                 uint32_t seg, uint32_t c, uint32_t W, uint8_t* out_rec,
+                                 uint32_t* out_perm) {
+  __shared__ uint32_t s_f2[16], s_kb2, s_ib2;
+  constexpr uint32_t C = auto_seg_cap(2);
+  uint64_t* k0p = reinterpret_cast<uint64_t*>(buf + 16);
+  uint64_t* k1p = k0p + C;
+  uint32_t* ip = reinterpret_cast<uint32_t*>(k1p + C);
+  uint32_t (*red)[kSegThreads / 32] = reinterpret_cast<uint32_t (*)[kSegThreads / 32]>(ip + C);
+  uint32_t lo[4] = {~0u, ~0u, ~0u, ~0u}, hi[4] = {0, 0, 0, 0}, imax = 0;
+  for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
+    const uint64_t a = k0p[i], b = k1p[i];
+    const uint32_t w[4] = {static_cast<uint32_t>(a >> 32), static_cast<uint32_t>(a),
+                           static_cast<uint32_t>(b >> 32), static_cast<uint32_t>(b)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lo[q] = __vminu4(lo[q], w[q]);
+      hi[q] = __vmaxu4(hi[q], w[q]);
+    }
+    imax = max(imax, ip[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lo[q] = __vminu4(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = __vmaxu4(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+    imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+  }
+  const uint32_t warp = threadIdx.x >> 5;
+  if (lane_id() == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      red[q][warp] = lo[q];
+      red[4 + q][warp] = hi[q];
+    }
+    red[8][warp] = imax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t l4[4] = {~0u, ~0u, ~0u, ~0u}, h4[4] = {0, 0, 0, 0}, m = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+      for (int q = 0; q < 4; ++q) {
+        l4[q] = __vminu4(l4[q], red[q][w]);
+        h4[q] = __vmaxu4(h4[q], red[4 + q][w]);
+      }
+      m = max(m, red[8][w]);
+    }
+    uint32_t off = 0;
+    for (int p = 15; p >= 0; --p) {
+      const uint32_t l = (l4[p >> 2] >> (24 - 8 * (p & 3))) & 255u;
+      const uint32_t h = (h4[p >> 2] >> (24 - 8 * (p & 3))) & 255u;
+      const uint32_t wdt = h > l ? 32u - static_cast<uint32_t>(__clz(h - l)) : 0u;
+      s_f2[p] = l | ((off > 63u ? 63u : off) << 8) | (wdt << 16);
+      off += wdt;
+    }
+    s_kb2 = off;
+    s_ib2 = 32u - static_cast<uint32_t>(__clz(m | 1u));
+  }
+  __syncthreads();
+  const uint32_t kb = s_kb2, ib = s_ib2;
+  if (kb > 64) return false;  // block-uniform
+  const uint32_t ob = v.outbase[seg];
+  const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);
+  if (kb + ib <= 64) {
+    if (c <= 4 * kSegThreads) k2_radix<Item64, 4>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
+    else k2_radix<Item64, 8>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
+  } else {
+    if (c <= 4 * kSegThreads) k2_radix<Item96, 4>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
+    else k2_radix<Item96, 8>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
+  }
+  return true;
+}
+
 // One-key segment resident in buf: byte-wise minima and maxima of its keys
 // and the largest index give the byte code and the index width, then the
 // (code, index) items are sorted.
@@ -1252,7 +1392,10 @@ auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_re
     }
     switch (K) {
       case 1: sort_resident_k1(smem_raw, buf, v, seg, c, W, out_rec, out_perm); break;
-      case 2: sort_resident<2>(buf, v, seg, c, W, out_rec, out_perm); break;
+      case 2:
+        if (!sort_resident_k2(smem_raw, buf, v, seg, c, W, out_rec, out_perm))
+          sort_resident<2>(buf, v, seg, c, W, out_rec, out_perm);
+        break;
       case 3: sort_resident<3>(buf, v, seg, c, W, out_rec, out_perm); break;
       default: sort_resident<4>(buf, v, seg, c, W, out_rec, out_perm); break;
     }
@@ -1345,7 +1488,9 @@ static_assert(seg_plane_elems(1) * 12 <= kSegPlanesBytes && seg_plane_elems(2) *
 static_assert(16 * kSegThreads >= auto_seg_cap(1), "16 radix items per thread cover a one-key segment");
 static_assert(auto_seg_cap(1) * 12 + kRxHistBytes <= kSegPlanesBytes,
               "one-key planes and radix counters exceed the segment buffer");
-static_assert(5 * kRxWarps * 4 <= kRxHistBytes, "reduction scratch fits the radix counters");
+static_assert(9 * kRxWarps * 4 <= kRxHistBytes, "reduction scratch fits the radix counters");
+static_assert(auto_seg_cap(2) * 20 + kRxHistBytes <= kSegPlanesBytes, "two-key planes and radix counters fit");
+static_assert(auto_seg_cap(2) <= 8 * kSegThreads, "eight radix items per thread cover a two-key segment");
 static_assert(kMsdBuckets <= auto_seg_cap(1), "bucket counters fit the index plane");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
 // a few scalars; ptxas -v reports it) + 1 KB reserved each
