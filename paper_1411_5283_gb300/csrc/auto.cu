@@ -918,16 +918,43 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 }
 
 // Bucket pass for one-word items: the items (distinct integers below 2^bits)
-// are counted by their top kMsdBits bits in 2^kMsdBits shared counters,
-// scattered to their bucket's range, and every bucket is then sorted by one
-// thread (insertion sort).  Used when no bucket holds more than
-// kMsdMaxBucket items, which is the usual case: a segment's items spread over
-// their range because the index part is spread over the input.  Returns false,
-// with the items untouched in registers, when the counts are too uneven (then
-// the radix passes run).  cnt holds 2^kMsdBits words.
+// are counted by their top kMsdBits bits in 2^kMsdBits shared counters and
+// scattered to their bucket's range; then every bucket is sorted: one of at
+// most kMsdThread items by its lane (insertion sort), a larger one by the
+// whole warp (each lane ranks its items by counting the smaller values).
+// Used when no bucket holds more than kMsdMaxBucket items, the usual case: a
+// segment's byte-recoded items spread over their range.  Returns false, with
+// the items untouched in registers, when a bucket is larger (many copies of
+// one word share its code bits): then the radix passes run.  cnt holds
+// 2^kMsdBits words.
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
-constexpr uint32_t kMsdMaxBucket = 32;
+constexpr uint32_t kMsdThread = 8;
+constexpr uint32_t kMsdMaxBucket = 128;
+
+// The warp sorts a[0..m), m <= 32 P, by rank counting (every lane reads the
+// same value at a time: broadcasts).
+template <int P>
+__device__ __forceinline__ void warp_rank_sort(uint64_t* a, uint32_t m) {
+  const uint32_t lane = lane_id();
+  uint64_t v[P];
+  uint32_t rk[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    v[k] = lane + 32u * k < m ? a[lane + 32u * k] : ~0ull;
+    rk[k] = 0;
+  }
+  for (uint32_t j = 0; j < m; ++j) {
+    const uint64_t y = a[j];
+#pragma unroll
+    for (int k = 0; k < P; ++k) rk[k] += y < v[k] ? 1u : 0u;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < P; ++k)
+    if (lane + 32u * k < m) a[rk[k]] = v[k];
+  __syncwarp();
+}
 
 template <int E>
 __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t nr, uint32_t nv,
@@ -978,17 +1005,31 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
   for (int j = 0; j < E; ++j)
     if (j < nv) a[atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u)] = x[j].v;
   __syncthreads();
-  // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b))
-  for (uint32_t b = threadIdx.x; b < kMsdBuckets; b += kSegThreads) {
+  // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b)).
+  // Warp w takes buckets 32 at a time (lane l: bucket base + l).
+  for (uint32_t base = warp * 32; base < kMsdBuckets; base += kSegThreads) {
+    const uint32_t b = base + lane;
     const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
-    for (uint32_t i = lo + 1; i < hi; ++i) {
-      const uint64_t key = a[i];
-      uint32_t q = i;
-      while (q > lo && a[q - 1] > key) {
-        a[q] = a[q - 1];
-        --q;
+    if (hi - lo <= kMsdThread) {
+      for (uint32_t i = lo + 1; i < hi; ++i) {
+        const uint64_t key = a[i];
+        uint32_t q = i;
+        while (q > lo && a[q - 1] > key) {
+          a[q] = a[q - 1];
+          --q;
+        }
+        a[q] = key;
       }
-      a[q] = key;
+    }
+    uint32_t big = __ballot_sync(0xffffffffu, hi - lo > kMsdThread);
+    while (big) {
+      const uint32_t l = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t blo = __shfl_sync(0xffffffffu, lo, l), bhi = __shfl_sync(0xffffffffu, hi, l);
+      const uint32_t m = bhi - blo;  // warp-uniform
+      if (m <= 32) warp_rank_sort<1>(a + blo, m);
+      else if (m <= 64) warp_rank_sort<2>(a + blo, m);
+      else warp_rank_sort<kMsdMaxBucket / 32>(a + blo, m);
     }
   }
   __syncthreads();
