@@ -42,14 +42,11 @@ namespace bsort {
 
 namespace {
 
-constexpr uint32_t kPartThreads = 512;
-constexpr uint32_t kSplSmem = 110 * 1024;          // splitter table staged up to this size
 constexpr uint32_t kSegThreads = 512;
 // One cursor per 128-byte line: the partition's atomics then spread over all
 // L2 slices instead of piling onto the few lines a packed array would use.
 constexpr uint32_t kCursorStride = 32;
 
-// words per lane kept in flight by the partition pass (fewer for wide keys)
 
 // ---------------------------------------------------------------------------
 // Device view of the AUTO area
@@ -61,6 +58,7 @@ struct AutoHdr {
   uint32_t spl_bytes;       // bytes of the splitter table
   uint32_t samp_cnt[kBins]; // samples drawn per bucket (may exceed capacity)
   uint32_t total[kBins];    // words per length (the histogram of phase 2)
+  uint32_t bcur[kBins];     // staging slots taken per length bucket
 };
 
 struct AutoView {
@@ -72,6 +70,8 @@ struct AutoView {
   uint32_t* rcap;     // per segment: region capacity (elements)
   uint32_t* outbase;  // per segment: first output rank
   uint32_t* segL;     // per segment: its length bucket
+  uint64_t* stage64;  // per bucket L: K_L planes of its words' keys (count_L each)
+  uint32_t* stage32;  // per bucket L: its words' indices, at the bucket offset
   uint64_t* rbase;    // per segment: first u64 of its K key planes in the key area
   uint64_t* ibase;    // per segment: first u32 of its index plane in the index area
   uint64_t* area64;   // key area (keys A, B, C of the workspace, contiguous)
@@ -111,6 +111,12 @@ __host__ __device__ AutoView auto_view(const Ws& ws, uint32_t W) {
   v.outbase = reinterpret_cast<uint32_t*>(p + o);
   o += 4 * G;
   v.segL = reinterpret_cast<uint32_t*>(p + o);
+  o += 4 * G;
+  // staging planes: per bucket L, K_L key planes then (separately) the indices
+  o = align_up(o, 256);
+  v.stage64 = reinterpret_cast<uint64_t*>(p + o);
+  o += align_up(8 * (cap + 64) * KW, 256);
+  v.stage32 = reinterpret_cast<uint32_t*>(p + o);
   v.area64 = ws.keys[0];
   v.area32 = ws.idx[0];
   const uint64_t third = cap >= kAutoMinWords + 64 ? cap + kAutoSlack : 0;
@@ -629,38 +635,20 @@ struct __align__(16) PartPlan {
   uint64_t r64, r32;
 };
 
-// Key word k (big-endian, bytes past L zero) of word i, from its record.
-__device__ __forceinline__ uint64_t record_key(const uint8_t* rec, uint32_t W, uint32_t i, uint32_t L,
-                                               uint32_t k) {
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
-  return bswap64(__ldg(src + k)) & key_mask(L, k);
-}
-
-// Is splitter sp (whose first key word equals the element's) <= the element
-// (key words 1..K-1 read from the record, then the index)?  Multi-key ties
-// only: rare.
-__device__ __forceinline__ bool splitter_le_tie(const uint64_t* sk, const uint32_t* si, uint32_t ns,
-                                             uint32_t sp, uint32_t K, const uint8_t* rec,
-                                             uint32_t W, uint32_t i, uint32_t L) {
-  for (uint32_t k = 1; k < K; ++k) {
-    const uint64_t a = sk[k * ns + sp], b = record_key(rec, W, i, L, k);
-    if (a != b) return a < b;
-  }
-  return si[sp] <= i;
-}
-
-// Segment of word i (length L, K key words, first key word k0) in bucket
-// plan p: the number of splitters <= the element (keys, i), splitters sorted
-// ascending.  The first-byte directory narrows the search to [lo, hi]; every
-// lane of the warp takes the same number of halving steps (the warp's
-// largest range), so the search loop does not diverge.  All lanes call; a
-// lane with active == false gets p.seg0.
-__device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, const PartPlan& p, uint32_t K,
-                                                 uint64_t k0, bool active, const uint8_t* rec,
-                                                 uint32_t W, uint32_t i, uint32_t L) {
-  const uint32_t ns = p.g - 1;
-  const uint16_t* dir = reinterpret_cast<const uint16_t*>(tab + p.spl_off);
-  const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + p.spl_off + kDirBytes);
+// Segment (index within the bucket) of an element with K key words, first
+// key word k0 and input index i, in a bucket whose splitter table (directory,
+// key planes, indices) starts at tab and holds g - 1 splitters: the number of
+// splitters <= the element.  key(k) reads key word k >= 1, needed only when
+// the first words tie.  The first-byte directory narrows the search to
+// [lo, hi]; every lane of the warp takes the same number of halving steps
+// (the warp's largest range), so the loop does not diverge.  All lanes call;
+// a lane with active == false gets 0.
+template <typename KeyK>
+__device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, uint32_t g, uint32_t K,
+                                                 uint64_t k0, uint32_t i, bool active, KeyK key) {
+  const uint32_t ns = g - 1;
+  const uint16_t* dir = reinterpret_cast<const uint16_t*>(tab);
+  const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + kDirBytes);
   const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(K) * ns);
   // splitters below dir[c] have a smaller first byte (all <= the element),
   // those from dir[c+1] on a larger one
@@ -676,24 +664,119 @@ __device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, const PartP
       const uint32_t mid = (lo + hi + 1) >> 1, sp = mid - 1;  // is splitter mid-1 <= element ?
       const uint64_t a = sk[sp];
       bool le = a < k0;
-      if (a == k0) le = K == 1 ? si[sp] <= i : splitter_le_tie(sk, si, ns, sp, K, rec, W, i, L);
+      if (a == k0) {
+        if (K == 1) {
+          le = si[sp] <= i;
+        } else {
+          // multi-key tie on the first word (rare): later words, then the index
+          uint32_t k = 1;
+          uint64_t ak = 0, bk = 0;
+          for (; k < K; ++k) {
+            ak = sk[k * ns + sp];
+            bk = key(k);
+            if (ak != bk) break;
+          }
+          le = k < K ? ak < bk : si[sp] <= i;
+        }
+      }
       lo = le ? mid : lo;
       hi = le ? hi : mid - 1;
     }
   }
-  return p.seg0 + lo;
+  return lo;
 }
 
-// Words per lane in flight per iteration of the partition loop.
-constexpr uint32_t kPartWords = 2;
+// ---- 3a. length buckets -------------------------------------------------
+// Tiles of kBucketTile words: each tile counts its words per length in shared
+// memory (the count so far is a word's slot within its tile), reserves one
+// range per length with a single global atomic, and writes every word's key
+// words and index into its bucket's staging planes (bucket L: K_L key planes
+// of count_L words at key offset kb_L = sum over l < L of count_l K_l, the
+// indices at the bucket offset off[L]).  A tile's words of one length land in
+// one contiguous range, so the writes combine in L2.
+constexpr uint32_t kBucketThreads = 512;
+constexpr uint32_t kBucketPer = 4;
+constexpr uint32_t kBucketTile = kBucketThreads * kBucketPer;
 
-__global__ void __launch_bounds__(kPartThreads, 2)
-auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
-                      uint32_t n_cap, const uint32_t* __restrict__ d_n, uint32_t W,
-                      const uint32_t* __restrict__ d_off, int retry_pass, Ws ws, AutoView av) {
+// Key offsets kb[L] (u64 units) of the staging planes, from the offsets.
+__device__ __forceinline__ void stage_key_bases(const uint32_t* s_off, uint32_t W, uint32_t* kb) {
+  if (threadIdx.x == 0) {
+    uint32_t o = 0;
+    for (uint32_t L = 0; L <= W + 1; ++L) {
+      kb[L] = o;
+      if (L >= 1 && L <= W) o += (s_off[L + 1] - s_off[L]) * keys_for_len(L);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBucketThreads)
+auto_bucket_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
+                   uint32_t n_cap, const uint32_t* __restrict__ d_n, uint32_t W,
+                   const uint32_t* __restrict__ d_off, Ws ws, AutoView av) {
+  __shared__ uint32_t s_off[kMaxW + 2], kb[kMaxW + 2], cnt[kBins], base[kBins];
+  const AutoView& v = av;
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  stage_key_bases(s_off, W, kb);
+  const uint32_t n = word_count(n_cap, d_n);
+  for (uint32_t t0 = blockIdx.x * kBucketTile; t0 < n; t0 += gridDim.x * kBucketTile) {
+    if (threadIdx.x < kBins) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t L[kBucketPer], r[kBucketPer];
+    uint64_t k0[kBucketPer];
+    // lengths and first key words first: the record reads overlap the counting
+#pragma unroll
+    for (uint32_t q = 0; q < kBucketPer; ++q) {
+      const uint32_t i = t0 + q * kBucketThreads + threadIdx.x;
+      const uint32_t l = i < n ? len[i] : 0u;
+      L[q] = (l >= 1 && l <= W) ? l : 0u;  // bad lengths are flagged by the histogram
+      k0[q] = L[q] ? __ldg(reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W)) : 0ull;
+    }
+#pragma unroll
+    for (uint32_t q = 0; q < kBucketPer; ++q) r[q] = L[q] ? atomicAdd(&cnt[L[q]], 1u) : 0u;
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x <= W && cnt[threadIdx.x])
+      base[threadIdx.x] = atomicAdd(&v.hdr->bcur[threadIdx.x], cnt[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (uint32_t q = 0; q < kBucketPer; ++q) {
+      if (!L[q]) continue;
+      const uint32_t i = t0 + q * kBucketThreads + threadIdx.x, l = L[q];
+      const uint32_t count = s_off[l + 1] - s_off[l], dest = base[l] + r[q];
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
+      uint64_t* dk = v.stage64 + kb[l] + dest;
+      dk[0] = bswap64(k0[q]) & key_mask(l, 0);
+      for (uint32_t k = 1; k < keys_for_len(l); ++k)
+        dk[static_cast<uint64_t>(k) * count] = bswap64(__ldg(src + k)) & key_mask(l, k);
+      v.stage32[s_off[l] + dest] = i;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- 3b. segments ---------------------------------------------------------
+// Bucket-uniform tiles of kPartTile staged elements: every element finds its
+// segment, the tile counts its elements per segment in shared memory (the
+// count so far is an element's slot within the tile's run), reserves one run
+// per segment with a single global atomic on the segment's cursor, and writes
+// the elements.  The bucket's splitter table is staged in shared memory when
+// it fits.  A slot past the region's end only counts and raises the overflow
+// flag (the retry pass then runs on exact regions).
+constexpr uint32_t kPartThreads2 = 512;
+constexpr uint32_t kPartPer = 4;
+constexpr uint32_t kPartTile = kPartThreads2 * kPartPer;
+constexpr uint32_t kPartCounters = 8192;                  // segments per bucket counted in shared memory
+constexpr uint32_t kPartSplSmem = 72 * 1024;              // bucket splitter table staged up to this size
+constexpr size_t kPartSmem = kPartCounters * 4 + kPartSplSmem;
+
+__global__ void __launch_bounds__(kPartThreads2, 2)
+auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_pass, Ws ws,
+                      AutoView av) {
   extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
+  uint8_t* tabs = smem + kPartCounters * 4;
   __shared__ PartPlan plans[kMaxW + 1];
-  __shared__ uint32_t s_off[kMaxW + 2];
+  __shared__ uint32_t s_off[kMaxW + 2], kb[kMaxW + 2], tp[kMaxW + 2];
   const AutoView& v = av;
   if (retry_pass && v.hdr->retry == 0) return;
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
@@ -702,78 +785,131 @@ auto_partition_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict
     const BucketPlan bp = threadIdx.x ? plan_for(s_off, threadIdx.x, v.cap) : BucketPlan{};
     plans[threadIdx.x] = PartPlan{bp.g, bp.seg0, bp.spl_off, bp.cap, bp.r64, bp.r32};
   }
-  // splitter table: staged in shared memory when it fits
-  const uint32_t tb = v.hdr->spl_bytes;
-  const uint8_t* tab = v.spl;
-  if (tb <= kSplSmem) {
-    const uint4* src = reinterpret_cast<const uint4*>(v.spl);
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-    for (uint32_t i = threadIdx.x; i < tb / 16; i += blockDim.x) dst[i] = src[i];
-    tab = smem;
+  stage_key_bases(s_off, W, kb);
+  if (threadIdx.x == 0) {  // tile prefix: tiles of buckets below L
+    uint32_t o = 0;
+    for (uint32_t L = 0; L <= W + 1; ++L) {
+      tp[L] = o;
+      if (L >= 1 && L <= W) o += (s_off[L + 1] - s_off[L] + kPartTile - 1) / kPartTile;
+    }
   }
   __syncthreads();
-  const uint32_t n = word_count(n_cap, d_n);
-  const uint32_t lane = lane_id();
+  const uint32_t tiles = tp[W + 1];
+  uint32_t staged = 0;  // bucket whose splitter table is in shared memory
   bool overflow = false;
-  const uint32_t warps_total = gridDim.x * (blockDim.x / 32);
-  constexpr uint32_t step = 32 * kPartWords;
-  for (uint32_t base = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * step; base < n;
-       base += warps_total * step) {
-    uint32_t L[kPartWords], seg[kPartWords];
-    uint64_t k0[kPartWords];
-    // all loads first: kPartWords independent records per lane in flight
+  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    uint32_t L = 1;
+    while (L < W && tp[L + 1] <= t) ++L;  // block-uniform
+    const PartPlan p = plans[L];
+    const uint32_t K = keys_for_len(L), count = s_off[L + 1] - s_off[L];
+    const uint32_t e0 = (t - tp[L]) * kPartTile, m = min(kPartTile, count - e0);
+    const uint64_t* k0p = v.stage64 + kb[L];
+    const uint32_t* ipp = v.stage32 + s_off[L];
+    // the bucket's splitter table
+    const uint8_t* tab = v.spl + p.spl_off;
+    const uint32_t tb = p.g > 1 ? static_cast<uint32_t>(spl_bytes_of(p.g, K)) : 0u;
+    const bool tab_smem = tb <= kPartSplSmem;
+    if (tab_smem && tb && staged != L) {
+      __syncthreads();  // earlier readers of the staged table are done
+      const uint4* src = reinterpret_cast<const uint4*>(tab);
+      uint4* dst = reinterpret_cast<uint4*>(tabs);
+      for (uint32_t q = threadIdx.x; q < tb / 16; q += blockDim.x) dst[q] = src[q];
+      staged = L;
+    }
+    if (tab_smem) tab = tabs;
+    const bool local = p.g <= kPartCounters;
+    if (local)
+      for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) cnt[q] = 0;
+    __syncthreads();
+    // segment (within the bucket) and slot of every element: s << 16 | slot
+    uint32_t sr[kPartPer], idxs[kPartPer];
+    uint64_t key0s[kPartPer];
 #pragma unroll
-    for (uint32_t u = 0; u < kPartWords; ++u) {
-      const uint32_t i = base + u * 32 + lane;
-      const uint32_t l = i < n ? len[i] : 0u;
-      L[u] = l > W ? 0u : l;
-      k0[u] = L[u] ? __ldg(reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W)) : 0ull;
+    for (uint32_t q = 0; q < kPartPer; ++q) {
+      const uint32_t e = q * kPartThreads2 + threadIdx.x;
+      key0s[q] = e < m ? k0p[e0 + e] : 0ull;
+      idxs[q] = e < m ? ipp[e0 + e] : 0u;
     }
 #pragma unroll
-    for (uint32_t u = 0; u < kPartWords; ++u) {
-      const uint32_t i = base + u * 32 + lane;
-      const PartPlan p = plans[L[u]];  // plans[0]: no segments
-      k0[u] = bswap64(k0[u]) & key_mask(L[u] ? L[u] : 1u, 0);
-      const uint32_t sg = find_segment(tab, p, keys_for_len(L[u]), k0[u], p.g > 1, rec, W, i, L[u]);
-      seg[u] = L[u] ? sg : 0xFFFFFFFFu;
-    }
-    uint32_t peers[kPartWords], first[kPartWords];
-#pragma unroll
-    for (uint32_t u = 0; u < kPartWords; ++u) {
-      peers[u] = __match_any_sync(0xffffffffu, seg[u]);
-      first[u] = 0;
-      if (seg[u] != 0xFFFFFFFFu && lane == __ffs(peers[u]) - 1)
-        first[u] = atomicAdd(&v.cursor[seg[u] * kCursorStride], __popc(peers[u]));
-    }
-#pragma unroll
-    for (uint32_t u = 0; u < kPartWords; ++u) {
-      const uint32_t f = __shfl_sync(0xffffffffu, first[u], __ffs(peers[u]) - 1);
-      if (seg[u] == 0xFFFFFFFFu) continue;
-      const uint32_t i = base + u * 32 + lane;
-      const uint32_t pos = f + __popc(peers[u] & lanemask_lt());
-      const uint32_t K = keys_for_len(L[u]);
-      uint32_t rc;
-      uint64_t rb, ib;
-      if (!retry_pass) {
-        // optimistic layout: a pure function of the bucket plan
-        const PartPlan p = plans[L[u]];
-        const uint32_t j = seg[u] - p.seg0;
-        rc = p.cap;
-        rb = p.r64 + static_cast<uint64_t>(j) * p.cap * K;
-        ib = p.r32 + static_cast<uint64_t>(j) * p.cap;
-      } else {
-        rc = v.rcap[seg[u]];
-        rb = v.rbase[seg[u]];
-        ib = v.ibase[seg[u]];
+    for (uint32_t q = 0; q < kPartPer; ++q) {
+      const uint32_t e = q * kPartThreads2 + threadIdx.x;
+      const bool in = e < m;
+      const uint64_t key0 = key0s[q];
+      const uint32_t idx = idxs[q];
+      auto keyk = [&](uint32_t k) { return k0p[static_cast<uint64_t>(k) * count + e0 + e]; };
+      const uint32_t sg = p.g > 1 ? find_segment(tab, p.g, K, key0, idx, in, keyk) : 0u;
+      uint32_t slot = 0;
+      if (in) slot = local ? atomicAdd(&cnt[sg], 1u) : atomicAdd(&v.cursor[(p.seg0 + sg) * kCursorStride], 1u);
+      sr[q] = (in && local) ? (sg << 16 | slot) : 0xFFFFFFFFu;
+      if (!local && in) {
+        // no tile counting: the slot came from the segment's cursor directly
+        const uint32_t pos = slot;
+        uint32_t rc;
+        uint64_t rb, ib;
+        if (!retry_pass) {
+          rc = p.cap;
+          rb = p.r64 + static_cast<uint64_t>(sg) * p.cap * K;
+          ib = p.r32 + static_cast<uint64_t>(sg) * p.cap;
+        } else {
+          rc = v.rcap[p.seg0 + sg];
+          rb = v.rbase[p.seg0 + sg];
+          ib = v.ibase[p.seg0 + sg];
+        }
+        if (pos < rc) {
+          for (uint32_t k = 0; k < K; ++k)
+            v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = k0p[static_cast<uint64_t>(k) * count + e0 + e];
+          v.area32[ib + pos] = idx;
+        } else {
+          overflow = true;
+        }
       }
-      if (pos < rc) {
-        v.area64[rb + pos] = k0[u];
-        for (uint32_t k = 1; k < K; ++k) v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = record_key(rec, W, i, L[u], k);
-        v.area32[ib + pos] = i;
-      } else {
-        overflow = true;
+    }
+    if (local) {
+      __syncthreads();
+      // one run per segment the tile touches; the reservations of a thread
+      // are issued back to back
+      constexpr uint32_t per = kPartCounters / kPartThreads2;
+      uint32_t got[per];
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) {
+        const uint32_t q = k * kPartThreads2 + threadIdx.x;
+        const uint32_t c = q < p.g ? cnt[q] : 0u;
+        got[k] = c ? atomicAdd(&v.cursor[(p.seg0 + q) * kCursorStride], c) : 0u;
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < per; ++k) {
+        const uint32_t q = k * kPartThreads2 + threadIdx.x;
+        if (q < p.g) cnt[q] = got[k];
+      }
+      __syncthreads();
+#pragma unroll
+      for (uint32_t q = 0; q < kPartPer; ++q) {
+        if (sr[q] == 0xFFFFFFFFu) continue;
+        const uint32_t e = q * kPartThreads2 + threadIdx.x, sg = sr[q] >> 16;
+        const uint32_t pos = cnt[sg] + (sr[q] & 0xFFFFu);
+        uint32_t rc;
+        uint64_t rb, ib;
+        if (!retry_pass) {
+          // optimistic layout: a pure function of the bucket plan
+          rc = p.cap;
+          rb = p.r64 + static_cast<uint64_t>(sg) * p.cap * K;
+          ib = p.r32 + static_cast<uint64_t>(sg) * p.cap;
+        } else {
+          rc = v.rcap[p.seg0 + sg];
+          rb = v.rbase[p.seg0 + sg];
+          ib = v.ibase[p.seg0 + sg];
+        }
+        if (pos < rc) {
+          v.area64[rb + pos] = key0s[q];
+          for (uint32_t k = 1; k < K; ++k)
+            v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = k0p[static_cast<uint64_t>(k) * count + e0 + e];
+          v.area32[ib + pos] = idxs[q];
+        } else {
+          overflow = true;
+        }
       }
     }
+    __syncthreads();  // counters and staged table reused by the next tile
   }
   if (overflow) atomicExch(&v.hdr->overflow, 1u);
 }
@@ -1663,7 +1799,10 @@ __global__ void auto_offsets_kernel(uint32_t W, Ws ws, AutoView av, uint32_t* __
     off[L] = s;
   }
   if (L < kMaxW + 2) ws.hdr->final_buf[L] = 0;
-  if (L < kBins) v.hdr->samp_cnt[L] = 0;
+  if (L < kBins) {
+    v.hdr->samp_cnt[L] = 0;
+    v.hdr->bcur[L] = 0;
+  }
   if (L == 0) {
     v.hdr->overflow = 0;
     v.hdr->retry = 0;
@@ -1686,15 +1825,14 @@ static_assert(2 * (segsort_smem_bytes() + 256 + 1024) <= 228 * 1024, "two segsor
 
 int g_sm_count = 0;
 
-cudaError_t partition(const uint8_t* rec, const uint8_t* len, uint32_t n_cap, const uint32_t* d_n,
-                      uint32_t W, const uint32_t* d_off, const Ws& ws, const AutoView& v, int retry,
+cudaError_t partition(uint32_t W, const uint32_t* d_off, const Ws& ws, const AutoView& v, int retry,
                       cudaStream_t s) {
   static size_t set = 0;
-  cudaError_t e = ensure_smem(auto_partition_kernel, kSplSmem, &set);
+  cudaError_t e = ensure_smem(auto_partition_kernel, kPartSmem, &set);
   if (e != cudaSuccess) return e;
   const uint32_t grid = static_cast<uint32_t>(g_sm_count) * 2;
   BSORT_LAUNCH(retry ? "auto_partition_retry" : "auto_partition", auto_partition_kernel, grid,
-               kPartThreads, kSplSmem, s, rec, len, n_cap, d_n, W, d_off, retry, ws, v);
+               kPartThreads2, kPartSmem, s, W, d_off, retry, ws, v);
   return cudaGetLastError();
 }
 
@@ -1735,6 +1873,9 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   BSORT_LAUNCH("auto_sample", auto_sample_kernel, (samples + 255) / 256, 256, 0, s, rec, len,
                n_cap, d_n, W, d_off, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  BSORT_LAUNCH("auto_bucket", auto_bucket_kernel, static_cast<uint32_t>(g_sm_count) * 2, kBucketThreads,
+               0, s, rec, len, n_cap, d_n, W, d_off, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, s,
                d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1743,11 +1884,11 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, W, 288, 0, s, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = partition(rec, len, n_cap, d_n, W, d_off, ws, v, 0, s);
+  e = partition(W, d_off, ws, v, 0, s);
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_layout", auto_layout_kernel, 1, 1024, 0, s, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = partition(rec, len, n_cap, d_n, W, d_off, ws, v, 1, s);
+  e = partition(W, d_off, ws, v, 1, s);
   if (e != cudaSuccess) return e;
   BSORT_LAUNCH("auto_segsort", auto_segsort_kernel, static_cast<uint32_t>(g_sm_count) * 2,
                kSegThreads, segsort_smem_bytes(), s, W, ws, v, out_rec, out_perm);

@@ -78,7 +78,10 @@ constexpr size_t auto_bytes(uint64_t cap, uint32_t W) {
   // splitters (8 KW + 4), cursors (one 128-byte line each), four u32 and two
   // u64 tables per segment
   const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 128 + 4 * 4 + 8 * 2);
-  return align_up(4096 + samples + tables + (16 + kAutoDirBytes) * kBins + 4096, 256);
+  // staging planes of the length buckets (keys, indices), in workspaces the
+  // sample sort runs in
+  const size_t stage = cap >= kAutoMinWords + 64 ? (cap + 64) * (8 * (W / 8) + 4) : 0;
+  return align_up(4096 + samples + tables + (16 + kAutoDirBytes) * kBins + 4096 + stage + 512, 256);
 }
 
 // Layout for a plane capacity of `cap` elements (a multiple of 64).
