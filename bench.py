@@ -38,14 +38,17 @@ SEED = 2
 # reported only while the sources still match (else null).
 NCU_TRAFFIC = {
     # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
-    # cut of the table (65.61 + 108.03 MB), x4 for 16,777,216 words; a lower
-    # bound: at 4M words part of the partition output is still in L2
-    "auto_segsort": {"bytes": 4 * (65.61e6 + 108.03e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8a3e97dffb76",
-                                 "paper_1411_5283_gb300/csrc/common.cuh": "03f6103478f2"}},
-    "auto_partition": {"bytes": 4 * (139.0e6 + 28.06e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8a3e97dffb76",
-                                   "paper_1411_5283_gb300/csrc/common.cuh": "03f6103478f2"}},
+    # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
+    # part of each kernel's output is still in L2 when the next one reads it
+    "auto_segsort": {"bytes": 4 * (57.94e6 + 112.81e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "29f563aaab8c",
+                                 "paper_1411_5283_gb300/csrc/common.cuh": "38eecab4c963"}},
+    "auto_partition": {"bytes": 4 * (55.26e6 + 6.78e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "29f563aaab8c",
+                                   "paper_1411_5283_gb300/csrc/common.cuh": "38eecab4c963"}},
+    "auto_bucket": {"bytes": 4 * (139.1e6 + 26.65e6),
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "29f563aaab8c",
+                                "paper_1411_5283_gb300/csrc/common.cuh": "38eecab4c963"}},
 }
 
 
@@ -155,9 +158,11 @@ def kernel_bytes(hist: np.ndarray, n: int, Wd: int, tile: int) -> dict:
         "tile_bitonic": 2 * int(elem.sum()),                  # read + write every element
         "tile_odd_even": 2 * int(elem.sum()),
         "gather": int(elem.sum()) + n * (Wd + 4),             # read keys+idx, write rec+perm
-        # sample sort: partition reads rec+len and writes elements into segments;
-        # segsort reads the elements and writes the final records + permutation
-        "auto_partition": n * (Wd + 1) + int(elem.sum()),
+        # sample sort: the bucket pass reads rec+len and writes the staged
+        # elements; partition reads them and writes them into segments; segsort
+        # reads the segments and writes the final records + permutation
+        "auto_bucket": n * (Wd + 1) + int(elem.sum()),
+        "auto_partition": 2 * int(elem.sum()),
         "auto_segsort": int(elem.sum()) + n * (Wd + 4),
     }
     merge = 0
