@@ -1203,17 +1203,26 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 // Bucket pass for one-word items: the items (distinct integers below 2^bits)
 // are counted by their top kMsdBits bits in 2^kMsdBits shared counters and
 // scattered to their bucket's range; then every bucket is sorted: one of at
-// most kMsdThread items by its lane (insertion sort), a larger one by the
-// whole warp (each lane ranks its items by counting the smaller values).
-// Used when no bucket holds more than kMsdMaxBucket items, the usual case: a
-// segment's byte-recoded items spread over their range.  Returns false, with
-// the items untouched in registers, when a bucket is larger (many copies of
-// one word share its code bits): then the radix passes run.  cnt holds
-// 2^kMsdBits words.
+// most kMsdThread items by its lane (insertion sort), one of at most
+// kMsdMaxBucket by the whole warp (each lane ranks its items by counting the
+// smaller values).  A larger bucket (copies of a frequent word share their
+// code bits) is listed and split again by the whole block: counted on the
+// kMsd2Bits bits below the highest bit in which its items differ, its
+// sub-buckets sorted or listed the same way, until the list is empty.
+// Returns false, with the items untouched in registers, when a bucket holds
+// more than kMsdScratch items: then the radix passes run.  cnt holds
+// 2^kMsdBits words; aux holds kMsdAuxWords words.
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
 constexpr uint32_t kMsdThread = 8;
 constexpr uint32_t kMsdMaxBucket = 128;
+constexpr uint32_t kMsd2Bits = 10;
+constexpr uint32_t kMsd2Buckets = 1u << kMsd2Bits;
+// a split bucket is copied into the counter words the sub-counters leave free
+constexpr uint32_t kMsdScratch = (kMsdBuckets - kMsd2Buckets) / 2;
+// listed buckets are disjoint and larger than kMsdMaxBucket
+constexpr uint32_t kMsdList = auto_seg_cap(1) / (kMsdMaxBucket + 1) + 1;
+constexpr uint32_t kMsdAuxWords = 4 * kRxWarps + kMsdList + 1;  // warp minima and maxima, list, its size
 
 // The warp sorts a[0..m), m <= 32 P, by rank counting (every lane reads the
 // same value at a time: broadcasts).
@@ -1239,12 +1248,131 @@ __device__ __forceinline__ void warp_rank_sort(uint64_t* a, uint32_t m) {
   __syncwarp();
 }
 
+// Sorts the buckets of a counting pass over a[0..) (cnt[b] = end of bucket b,
+// nb buckets, a multiple of 32): warp w takes buckets 32 at a time, lane l
+// bucket base + l; a bucket of at most kMsdThread items is sorted by its
+// lane, one of at most kMsdMaxBucket by the warp, a larger one is appended
+// to list as (base0 + start) | size << 16.
+__device__ __forceinline__ void sort_buckets(uint64_t* a, const uint32_t* cnt, uint32_t nb,
+                                             uint32_t base0, uint32_t* list, uint32_t* n_list) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  for (uint32_t base = warp * 32; base < nb; base += kSegThreads) {
+    const uint32_t b = base + lane;
+    const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
+    if (hi - lo <= kMsdThread) {
+      for (uint32_t i = lo + 1; i < hi; ++i) {
+        const uint64_t key = a[i];
+        uint32_t q = i;
+        while (q > lo && a[q - 1] > key) {
+          a[q] = a[q - 1];
+          --q;
+        }
+        a[q] = key;
+      }
+    } else if (hi - lo > kMsdMaxBucket) {
+      list[atomicAdd(n_list, 1u)] = (base0 + lo) | ((hi - lo) << 16);
+    }
+    uint32_t mid = __ballot_sync(0xffffffffu, hi - lo > kMsdThread && hi - lo <= kMsdMaxBucket);
+    while (mid) {
+      const uint32_t l = __ffs(mid) - 1;
+      mid &= mid - 1;
+      const uint32_t blo = __shfl_sync(0xffffffffu, lo, l), bhi = __shfl_sync(0xffffffffu, hi, l);
+      const uint32_t m = bhi - blo;  // warp-uniform
+      if (m <= 32) warp_rank_sort<1>(a + blo, m);
+      else if (m <= 64) warp_rank_sort<2>(a + blo, m);
+      else warp_rank_sort<kMsdMaxBucket / 32>(a + blo, m);
+    }
+  }
+}
+
+// Splits the listed buckets until none is left (the list is read after a
+// barrier).  The counter area holds the copy of the bucket being split
+// (kMsdScratch items) and its kMsd2Buckets sub-counters.  The items of a
+// bucket are distinct: its minimum and maximum differ, the kMsd2Bits window
+// ending at their highest differing bit holds at least two digits, and every
+// sub-bucket shares one more bit than its parent, so the splitting ends.
+__device__ __forceinline__ void split_buckets(uint64_t* a, uint32_t* area, uint32_t* aux,
+                                              uint32_t* warp_tmp) {
+  uint64_t* scratch = reinterpret_cast<uint64_t*>(area);
+  uint32_t* sub = area + 2 * kMsdScratch;
+  uint64_t* mm = reinterpret_cast<uint64_t*>(aux);  // warp minima, then maxima
+  uint32_t* list = aux + 4 * kRxWarps;
+  uint32_t* n_list = list + kMsdList;
+  constexpr uint32_t per = kMsd2Buckets / kSegThreads;  // sub-counters per thread
+  static_assert(per * kSegThreads == kMsd2Buckets, "sub-counters split evenly over the threads");
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  for (;;) {
+    const uint32_t t = *n_list;  // block-uniform
+    if (t == 0) break;
+    const uint32_t e = list[t - 1];
+    const uint32_t lo = e & 0xFFFFu, m = e >> 16;
+    __syncthreads();  // the entry is read before it is replaced
+    if (threadIdx.x == 0) *n_list = t - 1;
+    uint64_t vmin = ~0ull, vmax = 0;
+    for (uint32_t i = threadIdx.x; i < m; i += kSegThreads) {
+      const uint64_t y = a[lo + i];
+      scratch[i] = y;
+      vmin = y < vmin ? y : vmin;
+      vmax = y > vmax ? y : vmax;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < per; ++k) sub[threadIdx.x * per + k] = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t p = __shfl_xor_sync(0xffffffffu, vmin, o), q = __shfl_xor_sync(0xffffffffu, vmax, o);
+      vmin = p < vmin ? p : vmin;
+      vmax = q > vmax ? q : vmax;
+    }
+    if (lane == 0) {
+      mm[warp] = vmin;
+      mm[kRxWarps + warp] = vmax;
+    }
+    __syncthreads();
+    vmin = lane < kRxWarps ? mm[lane] : ~0ull;
+    vmax = lane < kRxWarps ? mm[kRxWarps + lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t p = __shfl_xor_sync(0xffffffffu, vmin, o), q = __shfl_xor_sync(0xffffffffu, vmax, o);
+      vmin = p < vmin ? p : vmin;
+      vmax = q > vmax ? q : vmax;
+    }
+    const uint32_t hb = 64u - static_cast<uint32_t>(__clzll(vmin ^ vmax));
+    const uint32_t sh = hb > kMsd2Bits ? hb - kMsd2Bits : 0u;
+    for (uint32_t i = threadIdx.x; i < m; i += kSegThreads)
+      atomicAdd(&sub[static_cast<uint32_t>(scratch[i] >> sh) & (kMsd2Buckets - 1)], 1u);
+    __syncthreads();
+    uint32_t c[per], sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < per; ++k) {
+      c[k] = sub[threadIdx.x * per + k];
+      sum += c[k];
+    }
+    const uint32_t inc = warp_inclusive_scan(sum);
+    if (lane == 31) warp_tmp[warp] = inc;
+    __syncthreads();
+    const uint32_t tw = lane < kRxWarps ? warp_tmp[lane] : 0u;
+    const uint32_t tupto = warp_inclusive_scan(tw);
+    uint32_t run = __shfl_sync(0xffffffffu, tupto - tw, warp) + inc - sum;
+#pragma unroll
+    for (uint32_t k = 0; k < per; ++k) {
+      sub[threadIdx.x * per + k] = run;  // sub-bucket start, then its cursor
+      run += c[k];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += kSegThreads) {
+      const uint64_t y = scratch[i];
+      a[lo + atomicAdd(&sub[static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1)], 1u)] = y;
+    }
+    __syncthreads();
+    sort_buckets(a + lo, sub, kMsd2Buckets, lo, list, n_list);
+    __syncthreads();
+  }
+}
+
 template <int E>
-__device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t nr, uint32_t nv,
-                                                  uint32_t p0, uint32_t bits, uint64_t* a,
-                                                  uint32_t* cnt, uint32_t* warp_tmp) {
-  (void)nr;
-  (void)p0;
+__device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t nv, uint32_t bits,
+                                                  uint64_t* a, uint32_t* cnt, uint32_t* warp_tmp,
+                                                  uint32_t* aux) {
   const uint32_t sh = bits > kMsdBits ? bits - kMsdBits : 0u;
   constexpr uint32_t per = kMsdBuckets / kSegThreads;  // counters per thread
   static_assert(per * kSegThreads == kMsdBuckets, "counters split evenly over the threads");
@@ -1276,46 +1404,24 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
   uint32_t tm = lane < kRxWarps ? warp_tmp[kRxWarps + lane] : 0u;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tm = max(tm, __shfl_xor_sync(0xffffffffu, tm, o));
-  if (tm > kMsdMaxBucket) return false;  // block-uniform
+  if (tm > kMsdScratch) return false;  // block-uniform
   uint32_t run = __shfl_sync(0xffffffffu, tupto - tw, warp) + inc - sum;
 #pragma unroll
   for (uint32_t k = 0; k < per; ++k) {
     mine[k] = run;  // bucket start, then its cursor
     run += v[k];
   }
+  uint32_t* n_list = aux + 4 * kRxWarps + kMsdList;
+  if (threadIdx.x == 0) *n_list = 0;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
     if (j < nv) a[atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u)] = x[j].v;
   __syncthreads();
-  // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b)).
-  // Warp w takes buckets 32 at a time (lane l: bucket base + l).
-  for (uint32_t base = warp * 32; base < kMsdBuckets; base += kSegThreads) {
-    const uint32_t b = base + lane;
-    const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
-    if (hi - lo <= kMsdThread) {
-      for (uint32_t i = lo + 1; i < hi; ++i) {
-        const uint64_t key = a[i];
-        uint32_t q = i;
-        while (q > lo && a[q - 1] > key) {
-          a[q] = a[q - 1];
-          --q;
-        }
-        a[q] = key;
-      }
-    }
-    uint32_t big = __ballot_sync(0xffffffffu, hi - lo > kMsdThread);
-    while (big) {
-      const uint32_t l = __ffs(big) - 1;
-      big &= big - 1;
-      const uint32_t blo = __shfl_sync(0xffffffffu, lo, l), bhi = __shfl_sync(0xffffffffu, hi, l);
-      const uint32_t m = bhi - blo;  // warp-uniform
-      if (m <= 32) warp_rank_sort<1>(a + blo, m);
-      else if (m <= 64) warp_rank_sort<2>(a + blo, m);
-      else warp_rank_sort<kMsdMaxBucket / 32>(a + blo, m);
-    }
-  }
+  // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b))
+  sort_buckets(a, cnt, kMsdBuckets, 0u, aux + 4 * kRxWarps, n_list);
   __syncthreads();
+  if (tm > kMsdMaxBucket) split_buckets(a, cnt, aux, warp_tmp);  // block-uniform
   return true;
 }
 
@@ -1346,7 +1452,7 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
   // byte-recoded keys spread their top bits: the bucket pass is tried first
   if constexpr (sizeof(It) == sizeof(Item64)) {
     if (bucket_cnt && bits > 8 &&
-        bucket_sort_items<E>(x, nr, nv, p0, bits, st.a, bucket_cnt, warp_tmp))
+        bucket_sort_items<E>(x, nv, bits, st.a, bucket_cnt, warp_tmp, reinterpret_cast<uint32_t*>(hist)))
       return;
   }
   uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
@@ -1819,6 +1925,9 @@ static_assert(9 * kRxWarps * 4 <= kRxHistBytes, "reduction scratch fits the radi
 static_assert(auto_seg_cap(2) * 20 + kRxHistBytes <= kSegPlanesBytes, "two-key planes and radix counters fit");
 static_assert(auto_seg_cap(2) <= 8 * kSegThreads, "eight radix items per thread cover a two-key segment");
 static_assert(kMsdBuckets <= auto_seg_cap(1), "bucket counters fit the index plane");
+static_assert(kMsdAuxWords * 4 <= kRxWarps * kRxDigits * sizeof(uint16_t), "split list fits the radix counters");
+static_assert(2 * kMsdScratch + kMsd2Buckets <= kMsdBuckets && kMsdScratch < 65536 && auto_seg_cap(1) <= 65536,
+              "split copy and sub-counters fit the counter area; list entries pack start and size");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
 // a few scalars; ptxas -v reports it) + 1 KB reserved each
 static_assert(2 * (segsort_smem_bytes() + 256 + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");

@@ -108,6 +108,51 @@ def test_auto_unrepresentative_sample_takes_exact_retry(env):
     assert_same_answer(out_rec, out_perm, off, expect, n)
 
 
+def test_auto_frequent_words_split_their_buckets(env):
+    """Three frequent four-letter words (70% of the words, two of them one
+    letter apart) among random ones: the segments at the edges of their runs
+    hold a few hundred to a few thousand copies in one bucket of the first
+    counting pass, which the block splits again on lower bits, down to the
+    index bits that tell copies apart."""
+    torch, bs, orc = env
+    n, W = 400_000, 8
+    rng = np.random.default_rng(17)
+    rec = np.zeros((n, W), np.uint8)
+    rec[:, :4] = rng.integers(ord("a"), ord("z") + 1, size=(n, 4), dtype=np.uint8)
+    pick = rng.random(n)
+    for word, lo, hi in ((b"abca", 0.0, 0.40), (b"abcb", 0.40, 0.60), (b"abda", 0.60, 0.70)):
+        rec[(pick >= lo) & (pick < hi), :4] = np.frombuffer(word, np.uint8)
+    ln = np.full(n, 4, np.uint8)
+    expect = orc.stable_sort(orc.Words(rec, ln))
+    s, (out_rec, out_perm, off) = run(env, rec, ln)
+    assert s.status() == 0
+    assert_same_answer(out_rec, out_perm, off, expect, n)
+
+
+def test_auto_frequent_word_missed_by_sample_overfills_a_bucket(env):
+    """4,000 copies of one word, all at positions the stratified sample skips,
+    among random words: the segment that receives them stays resident but one
+    bucket of the first counting pass holds more items than the split copy
+    area, so the segment takes the radix passes."""
+    torch, bs, orc = env
+    n, W = 120_000, 8
+    rng = np.random.default_rng(5)
+    rec = np.zeros((n, W), np.uint8)
+    rec[:, :4] = rng.integers(ord("a"), ord("z") + 1, size=(n, 4), dtype=np.uint8)
+    sampled = np.zeros(n, bool)
+    for s in range((n + 31) // 32):
+        i = s * 32 + (_mix64((s + 0x9E3779B97F4A7C15) & M64) & 31)
+        if i < n:
+            sampled[i] = True
+    free = np.flatnonzero(~sampled)
+    rec[rng.choice(free, 4000, replace=False), :4] = np.frombuffer(b"mmmm", np.uint8)
+    ln = np.full(n, 4, np.uint8)
+    expect = orc.stable_sort(orc.Words(rec, ln))
+    s, (out_rec, out_perm, off) = run(env, rec, ln)
+    assert s.status() == 0
+    assert_same_answer(out_rec, out_perm, off, expect, n)
+
+
 def test_auto_equals_merge_and_odd_even(env):
     torch, bs, orc = env
     rec, ln = synth.large_records(11, 150_000, 32)
