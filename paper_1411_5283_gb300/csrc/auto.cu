@@ -1618,6 +1618,59 @@ __device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32
   __syncthreads();
 }
 
+// Warp 0 combines the per-warp byte-wise minima and maxima of a segment's
+// keys (NQ 32-bit words of 4 bytes each: minima in red[0..NQ), maxima in
+// red[NQ..2NQ), the largest index in red[2NQ]) and writes the byte code's
+// fields: lane p < 4 NQ the field of byte position p (lo_p | offset_p << 8 |
+// width_p << 16; the offset is the summed width of the positions after p,
+// capped at 63), lane 0 the code width kb and the index width ib.
+template <int NQ>
+__device__ __forceinline__ void byte_fields(uint32_t (*red)[kRxWarps], uint32_t* f, uint32_t* kb,
+                                            uint32_t* ib) {
+  constexpr uint32_t P = 4 * NQ;
+  static_assert(P <= kRxWarps && kRxWarps <= 32, "one lane per position and per warp");
+  const uint32_t l = lane_id();
+  uint32_t lo[NQ], hi[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    lo[q] = l < kRxWarps ? red[q][l] : ~0u;
+    hi[q] = l < kRxWarps ? red[NQ + q][l] : 0u;
+  }
+  uint32_t m = l < kRxWarps ? red[2 * NQ][l] : 0u;
+#pragma unroll
+  for (uint32_t o = kRxWarps / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      lo[q] = __vminu4(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = __vmaxu4(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  const uint32_t p = l & (P - 1), sh = 24 - 8 * (p & 3);
+  uint32_t lw = lo[0], hw = hi[0];
+#pragma unroll
+  for (int q = 1; q < NQ; ++q) {
+    if ((p >> 2) == static_cast<uint32_t>(q)) {
+      lw = lo[q];
+      hw = hi[q];
+    }
+  }
+  const uint32_t lb = (lw >> sh) & 255u, hb = (hw >> sh) & 255u;
+  const uint32_t wdt = hb > lb ? 32u - static_cast<uint32_t>(__clz(hb - lb)) : 0u;
+  uint32_t s = wdt;  // summed width of positions p .. P-1
+#pragma unroll
+  for (uint32_t d = 1; d < P; d <<= 1) {
+    const uint32_t t = __shfl_down_sync(0xffffffffu, s, d);
+    if (p + d < P) s += t;
+  }
+  const uint32_t off = s - wdt;
+  if (l < P) f[p] = lb | ((off > 63u ? 63u : off) << 8) | (wdt << 16);
+  if (l == 0) {
+    *kb = s;
+    *ib = 32u - static_cast<uint32_t>(__clz(m | 1u));
+  }
+}
+
 // Two-key segment resident in buf: byte-wise minima and maxima over the 16 key
 // bytes; a code of at most 64 bits takes the item sort, a wider one the
 // bitonic network.  Returns false when the code is too wide.
@@ -1661,26 +1714,7 @@ __device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const A
     red[8][warp] = imax;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t l4[4] = {~0u, ~0u, ~0u, ~0u}, h4[4] = {0, 0, 0, 0}, m = 0;
-    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-      for (int q = 0; q < 4; ++q) {
-        l4[q] = __vminu4(l4[q], red[q][w]);
-        h4[q] = __vmaxu4(h4[q], red[4 + q][w]);
-      }
-      m = max(m, red[8][w]);
-    }
-    uint32_t off = 0;
-    for (int p = 15; p >= 0; --p) {
-      const uint32_t l = (l4[p >> 2] >> (24 - 8 * (p & 3))) & 255u;
-      const uint32_t h = (h4[p >> 2] >> (24 - 8 * (p & 3))) & 255u;
-      const uint32_t wdt = h > l ? 32u - static_cast<uint32_t>(__clz(h - l)) : 0u;
-      s_f2[p] = l | ((off > 63u ? 63u : off) << 8) | (wdt << 16);
-      off += wdt;
-    }
-    s_kb2 = off;
-    s_ib2 = 32u - static_cast<uint32_t>(__clz(m | 1u));
-  }
+  if (warp == 0) byte_fields<4>(red, s_f2, &s_kb2, &s_ib2);
   __syncthreads();
   const uint32_t kb = s_kb2, ib = s_ib2;
   if (kb > 64) return false;  // block-uniform
@@ -1735,27 +1769,7 @@ __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const A
     red[4][warp] = imax;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t a = ~0u, b = ~0u, x = 0, y = 0, m = 0;
-    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-      a = __vminu4(a, red[0][w]);
-      b = __vminu4(b, red[1][w]);
-      x = __vmaxu4(x, red[2][w]);
-      y = __vmaxu4(y, red[3][w]);
-      m = max(m, red[4][w]);
-    }
-    const uint64_t lo = (static_cast<uint64_t>(a) << 32) | b, hi = (static_cast<uint64_t>(x) << 32) | y;
-    uint32_t off = 0;
-    for (int p = 7; p >= 0; --p) {
-      const uint32_t l = static_cast<uint32_t>(lo >> (56 - 8 * p)) & 255u;
-      const uint32_t h = static_cast<uint32_t>(hi >> (56 - 8 * p)) & 255u;
-      const uint32_t wdt = h > l ? 32u - static_cast<uint32_t>(__clz(h - l)) : 0u;
-      s_f[p] = l | (off << 8) | (wdt << 16);
-      off += wdt;
-    }
-    s_kb = off;
-    s_ib = 32u - static_cast<uint32_t>(__clz(m | 1u));
-  }
+  if (warp == 0) byte_fields<2>(red, s_f, &s_kb, &s_ib);
   __syncthreads();
   ByteCode bc;
 #pragma unroll
