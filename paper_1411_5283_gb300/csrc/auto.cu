@@ -59,7 +59,9 @@ struct AutoHdr {
   uint32_t samp_cnt[kBins]; // samples drawn per bucket (may exceed capacity)
   uint32_t total[kBins];    // words per length (the histogram of phase 2)
   uint32_t bcur[kBins];     // staging slots taken per length bucket
+  uint32_t next_seg;        // segments handed out to the sorting CTAs
 };
+static_assert(sizeof(AutoHdr) <= 4096, "the header fits its page of the AUTO area");
 
 struct AutoView {
   AutoHdr* hdr;
@@ -1804,7 +1806,16 @@ auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_re
   __syncthreads();
   const uint32_t G = v.hdr->G;
   uint32_t phase = 0;
-  for (uint32_t seg = blockIdx.x; seg < G; seg += gridDim.x) {
+  __shared__ uint32_t s_next;
+  for (;;) {
+    // segments are handed out one at a time, longest words first (their
+    // segments cost the most per word), so the CTAs finish together
+    if (threadIdx.x == 0) s_next = atomicAdd(&v.hdr->next_seg, 1u);
+    __syncthreads();
+    const uint32_t t = s_next;
+    __syncthreads();
+    if (t >= G) break;
+    const uint32_t seg = G - 1 - t;
     const uint32_t c = seg_count(v, seg);
     const uint32_t L = v.segL[seg];
     const uint32_t K = keys_for_len(L);
@@ -1926,6 +1937,7 @@ __global__ void auto_offsets_kernel(uint32_t W, Ws ws, AutoView av, uint32_t* __
   if (L == 0) {
     v.hdr->overflow = 0;
     v.hdr->retry = 0;
+    v.hdr->next_seg = 0;
   }
 }
 
