@@ -1204,19 +1204,17 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 
 // Bucket pass for one-word items: the items (distinct integers below 2^bits)
 // are counted by their top kMsdBits bits in 2^kMsdBits shared counters and
-// scattered to their bucket's range; then every bucket is sorted: one of at
-// most kMsdThread items by its lane (insertion sort), one of at most
-// kMsdMaxBucket by the whole warp (each lane ranks its items by counting the
-// smaller values).  A larger bucket (copies of a frequent word share their
-// code bits) is listed and split again by the whole block: counted on the
-// kMsd2Bits bits below the highest bit in which its items differ, its
-// sub-buckets sorted or listed the same way, until the list is empty.
+// scattered to their bucket's range; then every item of a bucket of at most
+// kMsdMaxBucket items takes its place in the bucket by counting the smaller
+// items of its bucket.  A larger bucket (copies of a frequent word share
+// their code bits) is listed and split again by the whole block: counted on
+// the kMsd2Bits bits below the highest bit in which its items differ, its
+// sub-buckets placed or listed the same way, until the list is empty.
 // Returns false, with the items untouched in registers, when a bucket holds
 // more than kMsdScratch items: then the radix passes run.  cnt holds
 // 2^kMsdBits words; aux holds kMsdAuxWords words.
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
-constexpr uint32_t kMsdThread = 8;
 constexpr uint32_t kMsdMaxBucket = 128;
 constexpr uint32_t kMsd2Bits = 10;
 constexpr uint32_t kMsd2Buckets = 1u << kMsd2Bits;
@@ -1226,65 +1224,41 @@ constexpr uint32_t kMsdScratch = (kMsdBuckets - kMsd2Buckets) / 2;
 constexpr uint32_t kMsdList = auto_seg_cap(1) / (kMsdMaxBucket + 1) + 1;
 constexpr uint32_t kMsdAuxWords = 4 * kRxWarps + kMsdList + 1;  // warp minima and maxima, list, its size
 
-// The warp sorts a[0..m), m <= 32 P, by rank counting (every lane reads the
-// same value at a time: broadcasts).
-template <int P>
-__device__ __forceinline__ void warp_rank_sort(uint64_t* a, uint32_t m) {
-  const uint32_t lane = lane_id();
-  uint64_t v[P];
-  uint32_t rk[P];
-#pragma unroll
-  for (int k = 0; k < P; ++k) {
-    v[k] = lane + 32u * k < m ? a[lane + 32u * k] : ~0ull;
-    rk[k] = 0;
-  }
-  for (uint32_t j = 0; j < m; ++j) {
-    const uint64_t y = a[j];
-#pragma unroll
-    for (int k = 0; k < P; ++k) rk[k] += y < v[k] ? 1u : 0u;
-  }
-  __syncwarp();
-#pragma unroll
-  for (int k = 0; k < P; ++k)
-    if (lane + 32u * k < m) a[rk[k]] = v[k];
-  __syncwarp();
-}
-
-// Sorts the buckets of a counting pass over a[0..) (cnt[b] = end of bucket b,
-// nb buckets, a multiple of 32): warp w takes buckets 32 at a time, lane l
-// bucket base + l; a bucket of at most kMsdThread items is sorted by its
-// lane, one of at most kMsdMaxBucket by the warp, a larger one is appended
-// to list as (base0 + start) | size << 16.
-__device__ __forceinline__ void sort_buckets(uint64_t* a, const uint32_t* cnt, uint32_t nb,
+// Puts every item of a[0..m) at its place within its bucket.  The items lie
+// bucket by bucket (bucket d = digit(item) ends at cnt[d]).  Thread t takes
+// positions t, t + kSegThreads, ... (a warp: 32 neighbours, mostly of a few
+// buckets, whose items it reads as broadcasts), counts the smaller items of
+// the bucket and, after a barrier, stores its item at the bucket's start plus
+// that count.  A bucket of more than kMsdMaxBucket items stays in place and is
+// appended to list as (base0 + start) | size << 16 by the thread holding its
+// first item.
+template <int E, typename Digit>
+__device__ __forceinline__ void rank_buckets(uint64_t* a, uint32_t m, const uint32_t* cnt, Digit digit,
                                              uint32_t base0, uint32_t* list, uint32_t* n_list) {
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  for (uint32_t base = warp * 32; base < nb; base += kSegThreads) {
-    const uint32_t b = base + lane;
-    const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
-    if (hi - lo <= kMsdThread) {
-      for (uint32_t i = lo + 1; i < hi; ++i) {
-        const uint64_t key = a[i];
-        uint32_t q = i;
-        while (q > lo && a[q - 1] > key) {
-          a[q] = a[q - 1];
-          --q;
-        }
-        a[q] = key;
+  uint64_t v[E];
+  uint32_t dst[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const uint32_t i = threadIdx.x + k * kSegThreads;
+    v[k] = 0;
+    dst[k] = ~0u;
+    if (i < m) {
+      v[k] = a[i];
+      const uint32_t d = digit(v[k]);
+      const uint32_t lo = d ? cnt[d - 1] : 0u, hi = cnt[d];
+      if (hi - lo > kMsdMaxBucket) {
+        if (i == lo) list[atomicAdd(n_list, 1u)] = (base0 + lo) | ((hi - lo) << 16);
+      } else if (hi - lo > 1) {
+        uint32_t r = lo;
+        for (uint32_t q = lo; q < hi; ++q) r += a[q] < v[k] ? 1u : 0u;
+        dst[k] = r;
       }
-    } else if (hi - lo > kMsdMaxBucket) {
-      list[atomicAdd(n_list, 1u)] = (base0 + lo) | ((hi - lo) << 16);
-    }
-    uint32_t mid = __ballot_sync(0xffffffffu, hi - lo > kMsdThread && hi - lo <= kMsdMaxBucket);
-    while (mid) {
-      const uint32_t l = __ffs(mid) - 1;
-      mid &= mid - 1;
-      const uint32_t blo = __shfl_sync(0xffffffffu, lo, l), bhi = __shfl_sync(0xffffffffu, hi, l);
-      const uint32_t m = bhi - blo;  // warp-uniform
-      if (m <= 32) warp_rank_sort<1>(a + blo, m);
-      else if (m <= 64) warp_rank_sort<2>(a + blo, m);
-      else warp_rank_sort<kMsdMaxBucket / 32>(a + blo, m);
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < E; ++k)
+    if (dst[k] != ~0u) a[dst[k]] = v[k];
 }
 
 // Splits the listed buckets until none is left (the list is read after a
@@ -1366,7 +1340,9 @@ __device__ __forceinline__ void split_buckets(uint64_t* a, uint32_t* area, uint3
       a[lo + atomicAdd(&sub[static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1)], 1u)] = y;
     }
     __syncthreads();
-    sort_buckets(a + lo, sub, kMsd2Buckets, lo, list, n_list);
+    rank_buckets<(kMsdScratch + kSegThreads - 1) / kSegThreads>(
+        a + lo, m, sub, [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1); }, lo,
+        list, n_list);
     __syncthreads();
   }
 }
@@ -1421,7 +1397,8 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
     if (j < nv) a[atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u)] = x[j].v;
   __syncthreads();
   // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b))
-  sort_buckets(a, cnt, kMsdBuckets, 0u, aux + 4 * kRxWarps, n_list);
+  rank_buckets<E>(a, cnt[kMsdBuckets - 1], cnt, [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh); },
+                  0u, aux + 4 * kRxWarps, n_list);
   __syncthreads();
   if (tm > kMsdMaxBucket) split_buckets(a, cnt, aux, warp_tmp);  // block-uniform
   return true;
