@@ -60,6 +60,8 @@ struct AutoHdr {
   uint32_t total[kBins];    // words per length (the histogram of phase 2)
   uint32_t bcur[kBins];     // staging slots taken per length bucket
   uint32_t next_seg;        // segments handed out to the sorting CTAs
+  uint32_t band, bor;       // AND and OR of every byte inside a word: bounds of their range
+  uint32_t imax;            // largest word index
 };
 static_assert(sizeof(AutoHdr) <= 4096, "the header fits its page of the AUTO area");
 
@@ -72,6 +74,7 @@ struct AutoView {
   uint32_t* rcap;     // per segment: region capacity (elements)
   uint32_t* outbase;  // per segment: first output rank
   uint32_t* segL;     // per segment: its length bucket
+  uint32_t* segf;     // per segment: byte code fields, code width, index width (kSegFWords)
   uint64_t* stage64;  // per bucket L: K_L planes of its words' keys (count_L each)
   uint32_t* stage32;  // per bucket L: its words' indices, at the bucket offset
   uint64_t* rbase;    // per segment: first u64 of its K key planes in the key area
@@ -114,6 +117,8 @@ __host__ __device__ AutoView auto_view(const Ws& ws, uint32_t W) {
   o += 4 * G;
   v.segL = reinterpret_cast<uint32_t*>(p + o);
   o += 4 * G;
+  v.segf = reinterpret_cast<uint32_t*>(p + o);
+  o += 4 * kSegFWords * G;
   // staging planes: per bucket L, K_L key planes then (separately) the indices
   o = align_up(o, 256);
   v.stage64 = reinterpret_cast<uint64_t*>(p + o);
@@ -601,6 +606,66 @@ auto_spl_select_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, Au
   }
 }
 
+// Byte code records of a one- or two-key bucket's segments.  Segment q holds
+// the words between splitters q-1 and q (inclusive on the keys), so its keys
+// agree with both splitters up to the first byte position p0 where the two
+// differ: those positions are constant (width 0), position p0 spans the two
+// splitters' bytes, and every later position of the word the range of all
+// bytes inside words, [band, bor]; positions past the word are zero.  The
+// first segment has no lower splitter (band in every position), the last no
+// upper one (bor).  The index width covers the largest word index.  Every key
+// of the segment fits the fields, and the code keeps the key order.
+__device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L) {
+  const uint32_t band = v.hdr->band, bor = v.hdr->bor;
+  const uint32_t wl = bor > band ? 32u - static_cast<uint32_t>(__clz(bor - band)) : 0u;
+  const uint32_t ib = 32u - static_cast<uint32_t>(__clz(v.hdr->imax | 1u));
+  const uint32_t ns = p.g - 1;
+  const uint64_t* sk = reinterpret_cast<const uint64_t*>(v.spl + p.spl_off + kDirBytes);
+  const uint64_t lo_all = 0x0101010101010101ull * band, hi_all = 0x0101010101010101ull * bor;
+  for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) {
+    uint64_t lk[2], uk[2];
+#pragma unroll
+    for (uint32_t k = 0; k < 2; ++k) {
+      lk[k] = k < p.K && q > 0 ? sk[k * ns + q - 1] : lo_all;
+      uk[k] = k < p.K && q < ns ? sk[k * ns + q] : hi_all;
+    }
+    uint32_t fl[16];  // lo | width << 16
+    bool split = false;
+#pragma unroll
+    for (uint32_t pos = 0; pos < 16; ++pos) {
+      const uint32_t k = pos >> 3, sh = 56 - 8 * (pos & 7);
+      const uint32_t lb = static_cast<uint32_t>(lk[k] >> sh) & 255u;
+      const uint32_t ub = static_cast<uint32_t>(uk[k] >> sh) & 255u;
+      uint32_t lo = 0, w = 0;
+      if (pos < L && k < p.K) {
+        if (split) {
+          lo = band;
+          w = wl;
+        } else if (lb == ub) {
+          lo = lb;
+        } else {
+          // lb < ub, but for the all-ones splitters of an unsampled bucket,
+          // whose later segments stay empty
+          split = true;
+          lo = min(lb, ub);
+          w = 32u - static_cast<uint32_t>(__clz(max(lb, ub) - lo));
+        }
+      }
+      fl[pos] = lo | (w << 16);
+    }
+    uint32_t* f = v.segf + static_cast<size_t>(p.seg0 + q) * kSegFWords;
+    uint32_t off = 0;
+#pragma unroll
+    for (int pos = 15; pos >= 0; --pos) {
+      const uint32_t w = fl[pos] >> 16;
+      f[pos] = (fl[pos] & 255u) | ((off > 63u ? 63u : off) << 8) | (w << 16);
+      off += w;
+    }
+    f[16] = off;
+    f[17] = ib;
+  }
+}
+
 // (c) one CTA per bucket: directory dir[b] = number of splitters whose first
 // byte is below b (splitters are sorted, so their first bytes never decrease).
 __global__ void __launch_bounds__(288)
@@ -613,6 +678,7 @@ auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoV
   __syncthreads();
   if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
   __syncthreads();
+  if (p.K <= 2) segment_codes(v, p, L);
   if (p.g < 2) return;
   const uint32_t ns = p.g - 1, b = threadIdx.x;
   if (b > 256) return;
@@ -700,6 +766,15 @@ constexpr uint32_t kBucketThreads = 512;
 constexpr uint32_t kBucketPer = 4;
 constexpr uint32_t kBucketTile = kBucketThreads * kBucketPer;
 
+// Folds key word w (bytes past the word cleared by mask m) into the AND and
+// the OR of the bytes inside words.  Every such byte b has band <= b <= bor
+// (band's bits are a subset of b's, b's a subset of bor's); for letters the
+// bounds are as tight as the smallest and largest letter's in bit width.
+__device__ __forceinline__ void letter_bounds(uint64_t w, uint64_t m, uint64_t& band, uint64_t& bor) {
+  band &= w | ~m;  // bytes past the word read as all ones for the AND
+  bor |= w;
+}
+
 // Key offsets kb[L] (u64 units) of the staging planes, from the offsets.
 __device__ __forceinline__ void stage_key_bases(const uint32_t* s_off, uint32_t W, uint32_t* kb) {
   if (threadIdx.x == 0) {
@@ -721,6 +796,8 @@ auto_bucket_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
   __syncthreads();
   stage_key_bases(s_off, W, kb);
   const uint32_t n = word_count(n_cap, d_n);
+  uint64_t band = ~0ull, bor = 0;  // AND and OR of the bytes inside words
+  if (blockIdx.x == 0 && threadIdx.x == 0) v.hdr->imax = n ? n - 1 : 0;
   for (uint32_t t0 = blockIdx.x * kBucketTile; t0 < n; t0 += gridDim.x * kBucketTile) {
     if (threadIdx.x < kBins) cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -747,12 +824,29 @@ auto_bucket_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
       const uint32_t count = s_off[l + 1] - s_off[l], dest = base[l] + r[q];
       const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
       uint64_t* dk = v.stage64 + kb[l] + dest;
-      dk[0] = bswap64(k0[q]) & key_mask(l, 0);
-      for (uint32_t k = 1; k < keys_for_len(l); ++k)
-        dk[static_cast<uint64_t>(k) * count] = bswap64(__ldg(src + k)) & key_mask(l, k);
+      const uint64_t w0 = bswap64(k0[q]) & key_mask(l, 0);
+      dk[0] = w0;
+      letter_bounds(w0, key_mask(l, 0), band, bor);
+      for (uint32_t k = 1; k < keys_for_len(l); ++k) {
+        const uint64_t w = bswap64(__ldg(src + k)) & key_mask(l, k);
+        dk[static_cast<uint64_t>(k) * count] = w;
+        letter_bounds(w, key_mask(l, k), band, bor);
+      }
       v.stage32[s_off[l] + dest] = i;
     }
     __syncthreads();
+  }
+  band &= band >> 32;
+  band &= band >> 16;
+  band &= band >> 8;
+  bor |= bor >> 32;
+  bor |= bor >> 16;
+  bor |= bor >> 8;
+  const uint32_t a = __reduce_and_sync(0xffffffffu, static_cast<uint32_t>(band) & 255u);
+  const uint32_t o = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(bor) & 255u);
+  if (lane_id() == 0) {
+    if (a != 255u) atomicAnd(&v.hdr->band, a);
+    if (o != 0u) atomicOr(&v.hdr->bor, o);
   }
 }
 
@@ -1597,103 +1691,17 @@ __device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32
   __syncthreads();
 }
 
-// Warp 0 combines the per-warp byte-wise minima and maxima of a segment's
-// keys (NQ 32-bit words of 4 bytes each: minima in red[0..NQ), maxima in
-// red[NQ..2NQ), the largest index in red[2NQ]) and writes the byte code's
-// fields: lane p < 4 NQ the field of byte position p (lo_p | offset_p << 8 |
-// width_p << 16; the offset is the summed width of the positions after p,
-// capped at 63), lane 0 the code width kb and the index width ib.
-template <int NQ>
-__device__ __forceinline__ void byte_fields(uint32_t (*red)[kRxWarps], uint32_t* f, uint32_t* kb,
-                                            uint32_t* ib) {
-  constexpr uint32_t P = 4 * NQ;
-  static_assert(P <= kRxWarps && kRxWarps <= 32, "one lane per position and per warp");
-  const uint32_t l = lane_id();
-  uint32_t lo[NQ], hi[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    lo[q] = l < kRxWarps ? red[q][l] : ~0u;
-    hi[q] = l < kRxWarps ? red[NQ + q][l] : 0u;
-  }
-  uint32_t m = l < kRxWarps ? red[2 * NQ][l] : 0u;
-#pragma unroll
-  for (uint32_t o = kRxWarps / 2; o > 0; o >>= 1) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      lo[q] = __vminu4(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
-      hi[q] = __vmaxu4(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
-    }
-    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  }
-  const uint32_t p = l & (P - 1), sh = 24 - 8 * (p & 3);
-  uint32_t lw = lo[0], hw = hi[0];
-#pragma unroll
-  for (int q = 1; q < NQ; ++q) {
-    if ((p >> 2) == static_cast<uint32_t>(q)) {
-      lw = lo[q];
-      hw = hi[q];
-    }
-  }
-  const uint32_t lb = (lw >> sh) & 255u, hb = (hw >> sh) & 255u;
-  const uint32_t wdt = hb > lb ? 32u - static_cast<uint32_t>(__clz(hb - lb)) : 0u;
-  uint32_t s = wdt;  // summed width of positions p .. P-1
-#pragma unroll
-  for (uint32_t d = 1; d < P; d <<= 1) {
-    const uint32_t t = __shfl_down_sync(0xffffffffu, s, d);
-    if (p + d < P) s += t;
-  }
-  const uint32_t off = s - wdt;
-  if (l < P) f[p] = lb | ((off > 63u ? 63u : off) << 8) | (wdt << 16);
-  if (l == 0) {
-    *kb = s;
-    *ib = 32u - static_cast<uint32_t>(__clz(m | 1u));
-  }
-}
-
-// Two-key segment resident in buf: byte-wise minima and maxima over the 16 key
-// bytes; a code of at most 64 bits takes the item sort, a wider one the
-// bitonic network.  Returns false when the code is too wide.
+// Two-key segment resident in buf: a code (from the segment's record) of at
+// most 64 bits takes the item sort, a wider one the bitonic network.  Returns
+// false when the code is too wide.
 __device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
                                  uint32_t seg, uint32_t c, uint32_t W, uint8_t* out_rec,
                                  uint32_t* out_perm) {
   __shared__ uint32_t s_f2[16], s_kb2, s_ib2;
-  constexpr uint32_t C = auto_seg_cap(2);
-  uint64_t* k0p = reinterpret_cast<uint64_t*>(buf + 16);
-  uint64_t* k1p = k0p + C;
-  uint32_t* ip = reinterpret_cast<uint32_t*>(k1p + C);
-  uint32_t (*red)[kSegThreads / 32] = reinterpret_cast<uint32_t (*)[kSegThreads / 32]>(ip + C);
-  uint32_t lo[4] = {~0u, ~0u, ~0u, ~0u}, hi[4] = {0, 0, 0, 0}, imax = 0;
-  for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
-    const uint64_t a = k0p[i], b = k1p[i];
-    const uint32_t w[4] = {static_cast<uint32_t>(a >> 32), static_cast<uint32_t>(a),
-                           static_cast<uint32_t>(b >> 32), static_cast<uint32_t>(b)};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      lo[q] = __vminu4(lo[q], w[q]);
-      hi[q] = __vmaxu4(hi[q], w[q]);
-    }
-    imax = max(imax, ip[i]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      lo[q] = __vminu4(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
-      hi[q] = __vmaxu4(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
-    }
-    imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
-  }
-  const uint32_t warp = threadIdx.x >> 5;
-  if (lane_id() == 0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      red[q][warp] = lo[q];
-      red[4 + q][warp] = hi[q];
-    }
-    red[8][warp] = imax;
-  }
-  __syncthreads();
-  if (warp == 0) byte_fields<4>(red, s_f2, &s_kb2, &s_ib2);
+  const uint32_t* sf = v.segf + static_cast<size_t>(seg) * kSegFWords;
+  if (threadIdx.x < 16) s_f2[threadIdx.x] = __ldg(sf + threadIdx.x);
+  else if (threadIdx.x == 16) s_kb2 = __ldg(sf + 16);
+  else if (threadIdx.x == 17) s_ib2 = __ldg(sf + 17);
   __syncthreads();
   const uint32_t kb = s_kb2, ib = s_ib2;
   if (kb > 64) return false;  // block-uniform
@@ -1709,51 +1717,16 @@ __device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const A
   return true;
 }
 
-// One-key segment resident in buf: byte-wise minima and maxima of its keys
-// and the largest index give the byte code and the index width, then the
-// (code, index) items are sorted.
+// One-key segment resident in buf: its byte code (from the segment's record)
+// recodes the keys, then the (code, index) items are sorted.
 __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
                                  uint32_t seg, uint32_t c, uint32_t W, uint8_t* out_rec,
                                  uint32_t* out_perm) {
-  __shared__ uint32_t s_f[8], s_kb, s_ib;
-  constexpr uint32_t C = auto_seg_cap(1);
-  uint64_t* kp = reinterpret_cast<uint64_t*>(buf + 16);
-  uint32_t* ip = reinterpret_cast<uint32_t*>(kp + C);
-  // per-warp partial results in the (not yet used) radix counter area
-  uint32_t (*red)[kSegThreads / 32] = reinterpret_cast<uint32_t (*)[kSegThreads / 32]>(ip + C);
-  uint32_t lo_h = ~0u, lo_l = ~0u, hi_h = 0, hi_l = 0, imax = 0;
-  for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
-    const uint64_t k = kp[i];
-    const uint32_t h = static_cast<uint32_t>(k >> 32), l = static_cast<uint32_t>(k);
-    lo_h = __vminu4(lo_h, h);
-    lo_l = __vminu4(lo_l, l);
-    hi_h = __vmaxu4(hi_h, h);
-    hi_l = __vmaxu4(hi_l, l);
-    imax = max(imax, ip[i]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lo_h = __vminu4(lo_h, __shfl_xor_sync(0xffffffffu, lo_h, o));
-    lo_l = __vminu4(lo_l, __shfl_xor_sync(0xffffffffu, lo_l, o));
-    hi_h = __vmaxu4(hi_h, __shfl_xor_sync(0xffffffffu, hi_h, o));
-    hi_l = __vmaxu4(hi_l, __shfl_xor_sync(0xffffffffu, hi_l, o));
-    imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
-  }
-  const uint32_t warp = threadIdx.x >> 5;
-  if (lane_id() == 0) {
-    red[0][warp] = lo_h;
-    red[1][warp] = lo_l;
-    red[2][warp] = hi_h;
-    red[3][warp] = hi_l;
-    red[4][warp] = imax;
-  }
-  __syncthreads();
-  if (warp == 0) byte_fields<2>(red, s_f, &s_kb, &s_ib);
-  __syncthreads();
+  const uint32_t* sf = v.segf + static_cast<size_t>(seg) * kSegFWords;
   ByteCode bc;
 #pragma unroll
-  for (int p = 0; p < 8; ++p) bc.f[p] = s_f[p];
-  const uint32_t kb = s_kb, ib = s_ib;
+  for (int p = 0; p < 8; ++p) bc.f[p] = __ldg(sf + p);
+  const uint32_t kb = __ldg(sf + 16), ib = __ldg(sf + 17);
   const uint32_t ob = v.outbase[seg];
   const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);
   if (kb + ib <= 64) {
@@ -1915,6 +1888,8 @@ __global__ void auto_offsets_kernel(uint32_t W, Ws ws, AutoView av, uint32_t* __
     v.hdr->overflow = 0;
     v.hdr->retry = 0;
     v.hdr->next_seg = 0;
+    v.hdr->band = 255;
+    v.hdr->bor = 0;
   }
 }
 

@@ -66,6 +66,9 @@ __host__ __device__ constexpr uint32_t auto_sample_cap(uint32_t K, uint64_t cap)
                                                                  : (cap / 64 < 256 ? 256 : cap / 64)) /
       64 * 64);
 }
+// Per-segment byte code record of the sample sort: 16 position fields (lo |
+// offset << 8 | width << 16), the code width and the index width.
+constexpr uint32_t kSegFWords = 18;
 __host__ __device__ constexpr uint64_t auto_max_segments(uint64_t cap) {
   return cap / 1024 + 2 * kBins + 1;
 }
@@ -76,8 +79,8 @@ constexpr size_t auto_bytes(uint64_t cap, uint32_t W) {
     samples += static_cast<size_t>(auto_sample_cap(K, cap)) * (8 * K + 4);
   }
   // splitters (8 KW + 4), cursors (one 128-byte line each), four u32 and two
-  // u64 tables per segment
-  const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 128 + 4 * 4 + 8 * 2);
+  // u64 tables and the 18-word byte code record per segment
+  const size_t tables = auto_max_segments(cap) * (8 * (W / 8) + 4 + 128 + 4 * 4 + 8 * 2 + 4 * kSegFWords);
   // staging planes of the length buckets (keys, indices), in workspaces the
   // sample sort runs in
   const size_t stage = cap >= kAutoMinWords + 64 ? (cap + 64) * (8 * (W / 8) + 4) : 0;

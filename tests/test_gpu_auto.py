@@ -153,6 +153,20 @@ def test_auto_frequent_word_missed_by_sample_overfills_a_bucket(env):
     assert_same_answer(out_rec, out_perm, off, expect, n)
 
 
+@pytest.mark.parametrize("alphabet", [bytes(range(256)), b"q", b"pq"])
+def test_auto_byte_ranges(env, alphabet):
+    """Segment byte codes follow from the splitters and the range of all bytes
+    inside words: every byte value (fields of 8 bits, codes too wide for one
+    machine word), a single letter (every field empty) and two letters."""
+    torch, bs, orc = env
+    n, W = 200_000, 16
+    rec, ln = table(23, n, W, alphabet)
+    expect = orc.stable_sort(orc.Words(rec, ln))
+    s, (out_rec, out_perm, off) = run(env, rec, ln)
+    assert s.status() == 0
+    assert_same_answer(out_rec, out_perm, off, expect, n)
+
+
 def test_auto_equals_merge_and_odd_even(env):
     torch, bs, orc = env
     rec, ln = synth.large_records(11, 150_000, 32)
