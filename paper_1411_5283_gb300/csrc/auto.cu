@@ -622,7 +622,8 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
   const uint32_t ns = p.g - 1;
   const uint64_t* sk = reinterpret_cast<const uint64_t*>(v.spl + p.spl_off + kDirBytes);
   const uint64_t lo_all = 0x0101010101010101ull * band, hi_all = 0x0101010101010101ull * bor;
-  for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) {
+  const uint32_t step = gridDim.y * blockDim.x;
+  for (uint32_t q = blockIdx.y * blockDim.x + threadIdx.x; q < p.g; q += step) {
     uint64_t lk[2], uk[2];
 #pragma unroll
     for (uint32_t k = 0; k < 2; ++k) {
@@ -666,8 +667,11 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
   }
 }
 
-// (c) one CTA per bucket: directory dir[b] = number of splitters whose first
-// byte is below b (splitters are sorted, so their first bytes never decrease).
+// (c) grid (W, kSplDirCtas): the CTAs of bucket L write its segments' byte
+// code records; CTA (L-1, 0) also the directory dir[b] = number of splitters
+// whose first byte is below b (splitters are sorted, so their first bytes
+// never decrease).
+constexpr uint32_t kSplDirCtas = 4;
 __global__ void __launch_bounds__(288)
 auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
   __shared__ uint32_t s_off[kMaxW + 2];
@@ -679,7 +683,7 @@ auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoV
   if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
   __syncthreads();
   if (p.K <= 2) segment_codes(v, p, L);
-  if (p.g < 2) return;
+  if (p.g < 2 || blockIdx.y > 0) return;
   const uint32_t ns = p.g - 1, b = threadIdx.x;
   if (b > 256) return;
   uint16_t* dir = reinterpret_cast<uint16_t*>(v.spl + p.spl_off);
@@ -1306,7 +1310,7 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 // sub-buckets placed or listed the same way, until the list is empty.
 // Returns false, with the items untouched in registers, when a bucket holds
 // more than kMsdScratch items: then the radix passes run.  cnt holds
-// 2^kMsdBits words; aux holds kMsdAuxWords words.
+// 2^kMsdBits + 2^kMsdBits / 16 words; aux holds kMsdAuxWords words.
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
 constexpr uint32_t kMsdMaxBucket = 128;
@@ -1317,18 +1321,22 @@ constexpr uint32_t kMsdScratch = (kMsdBuckets - kMsd2Buckets) / 2;
 // listed buckets are disjoint and larger than kMsdMaxBucket
 constexpr uint32_t kMsdList = auto_seg_cap(1) / (kMsdMaxBucket + 1) + 1;
 constexpr uint32_t kMsdAuxWords = 4 * kRxWarps + kMsdList + 1;  // warp minima and maxima, list, its size
+// The counters, one padding word per 16, run kMsdBuckets / 16 words past the
+// counter area (into the next plane); the list lives this far into the radix
+// counter area, clear of them.
+constexpr uint32_t kMsdAuxOffset = 1024;
 
 // Puts every item of a[0..m) at its place within its bucket.  The items lie
 // bucket by bucket (bucket d = digit(item) ends at cnt[d]).  Thread t takes
 // positions t, t + kSegThreads, ... (a warp: 32 neighbours, mostly of a few
 // buckets, whose items it reads as broadcasts), counts the smaller items of
 // the bucket and, after a barrier, stores its item at the bucket's start plus
-// that count.  A bucket of more than kMsdMaxBucket items stays in place and is
+// that count.  Bucket d's end is cnt[slot(d)].  A bucket of more than kMsdMaxBucket items stays in place and is
 // appended to list as (base0 + start) | size << 16 by the thread holding its
 // first item.
-template <int E, typename Digit>
+template <int E, typename Digit, typename Slot>
 __device__ __forceinline__ void rank_buckets(uint64_t* a, uint32_t m, const uint32_t* cnt, Digit digit,
-                                             uint32_t base0, uint32_t* list, uint32_t* n_list) {
+                                             Slot slot, uint32_t base0, uint32_t* list, uint32_t* n_list) {
   uint64_t v[E];
   uint32_t dst[E];
 #pragma unroll
@@ -1339,7 +1347,7 @@ __device__ __forceinline__ void rank_buckets(uint64_t* a, uint32_t m, const uint
     if (i < m) {
       v[k] = a[i];
       const uint32_t d = digit(v[k]);
-      const uint32_t lo = d ? cnt[d - 1] : 0u, hi = cnt[d];
+      const uint32_t lo = d ? cnt[slot(d - 1)] : 0u, hi = cnt[slot(d)];
       if (hi - lo > kMsdMaxBucket) {
         if (i == lo) list[atomicAdd(n_list, 1u)] = (base0 + lo) | ((hi - lo) << 16);
       } else if (hi - lo > 1) {
@@ -1435,8 +1443,8 @@ __device__ __forceinline__ void split_buckets(uint64_t* a, uint32_t* area, uint3
     }
     __syncthreads();
     rank_buckets<(kMsdScratch + kSegThreads - 1) / kSegThreads>(
-        a + lo, m, sub, [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1); }, lo,
-        list, n_list);
+        a + lo, m, sub, [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1); },
+        [](uint32_t d) { return d; }, lo, list, n_list);
     __syncthreads();
   }
 }
@@ -1447,14 +1455,17 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
                                                   uint32_t* aux) {
   const uint32_t sh = bits > kMsdBits ? bits - kMsdBits : 0u;
   constexpr uint32_t per = kMsdBuckets / kSegThreads;  // counters per thread
-  static_assert(per * kSegThreads == kMsdBuckets, "counters split evenly over the threads");
-  uint32_t* mine = cnt + threadIdx.x * per;
+  static_assert(per == 16 && per * kSegThreads == kMsdBuckets, "16 counters per thread");
+  // thread t's counters (buckets 16 t .. 16 t + 15) start at word 17 t: the
+  // threads of a warp touch 32 different banks when they walk their counters
+  const auto slot = [](uint32_t b) { return b + (b >> 4); };
+  uint32_t* mine = cnt + threadIdx.x * (per + 1);
 #pragma unroll
   for (uint32_t k = 0; k < per; ++k) mine[k] = 0;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u);
+    if (j < nv) atomicAdd(&cnt[slot(static_cast<uint32_t>(x[j].v >> sh))], 1u);
   __syncthreads();
   // exclusive scan of the counts (thread t owns counters t*per .. t*per+per-1)
   uint32_t v[per], sum = 0, mx = 0;
@@ -1488,11 +1499,12 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) a[atomicAdd(&cnt[static_cast<uint32_t>(x[j].v >> sh)], 1u)] = x[j].v;
+    if (j < nv) a[atomicAdd(&cnt[slot(static_cast<uint32_t>(x[j].v >> sh))], 1u)] = x[j].v;
   __syncthreads();
-  // cnt[b] is now the end of bucket b; bucket b spans [end(b-1), end(b))
-  rank_buckets<E>(a, cnt[kMsdBuckets - 1], cnt, [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh); },
-                  0u, aux + 4 * kRxWarps, n_list);
+  // cnt[slot(b)] is now the end of bucket b; bucket b spans [end(b-1), end(b))
+  rank_buckets<E>(a, cnt[slot(kMsdBuckets - 1)], cnt,
+                  [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh); }, slot, 0u, aux + 4 * kRxWarps,
+                  n_list);
   __syncthreads();
   if (tm > kMsdMaxBucket) split_buckets(a, cnt, aux, warp_tmp);  // block-uniform
   return true;
@@ -1525,7 +1537,8 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
   // byte-recoded keys spread their top bits: the bucket pass is tried first
   if constexpr (sizeof(It) == sizeof(Item64)) {
     if (bucket_cnt && bits > 8 &&
-        bucket_sort_items<E>(x, nv, bits, st.a, bucket_cnt, warp_tmp, reinterpret_cast<uint32_t*>(hist)))
+        bucket_sort_items<E>(x, nv, bits, st.a, bucket_cnt, warp_tmp,
+                             reinterpret_cast<uint32_t*>(hist) + kMsdAuxOffset))
       return;
   }
   uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
@@ -1903,7 +1916,13 @@ static_assert(9 * kRxWarps * 4 <= kRxHistBytes, "reduction scratch fits the radi
 static_assert(auto_seg_cap(2) * 20 + kRxHistBytes <= kSegPlanesBytes, "two-key planes and radix counters fit");
 static_assert(auto_seg_cap(2) <= 8 * kSegThreads, "eight radix items per thread cover a two-key segment");
 static_assert(kMsdBuckets <= auto_seg_cap(1), "bucket counters fit the index plane");
-static_assert(kMsdAuxWords * 4 <= kRxWarps * kRxDigits * sizeof(uint16_t), "split list fits the radix counters");
+static_assert((kMsdAuxOffset + kMsdAuxWords) * 4 <= kRxWarps * kRxDigits * sizeof(uint16_t),
+              "split list fits the radix counters");
+// one-key segments: counters in the index plane and the first kMsdBuckets / 16
+// words of the radix counters; two-key segments: in key plane 1 and the first
+// words of the index plane
+static_assert(kMsdBuckets / 16 <= kMsdAuxOffset && kMsdBuckets / 16 <= auto_seg_cap(2),
+              "padded bucket counters stay clear of the split list");
 static_assert(2 * kMsdScratch + kMsd2Buckets <= kMsdBuckets && kMsdScratch < 65536 && auto_seg_cap(1) <= 65536,
               "split copy and sub-counters fit the counter area; list entries pack start and size");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
@@ -1969,7 +1988,7 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   BSORT_LAUNCH("auto_spl_select", auto_spl_select_kernel, dim3(W, kSplChunks), 1024, kSplSelectSmem,
                s, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, W, 288, 0, s, d_off, W, ws, v);
+  BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, dim3(W, kSplDirCtas), 288, 0, s, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = partition(W, d_off, ws, v, 0, s);
   if (e != cudaSuccess) return e;
