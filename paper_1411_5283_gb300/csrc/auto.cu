@@ -632,6 +632,7 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
     }
     uint32_t fl[16];  // lo | width << 16
     bool split = false;
+    uint32_t p0 = 7;  // first position where the bounds differ (7: none)
 #pragma unroll
     for (uint32_t pos = 0; pos < 16; ++pos) {
       const uint32_t k = pos >> 3, sh = 56 - 8 * (pos & 7);
@@ -648,6 +649,7 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
           // lb < ub, but for the all-ones splitters of an unsampled bucket,
           // whose later segments stay empty
           split = true;
+          p0 = pos;
           lo = min(lb, ub);
           w = 32u - static_cast<uint32_t>(__clz(max(lb, ub) - lo));
         }
@@ -664,6 +666,16 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
     }
     f[16] = off;
     f[17] = ib;
+    if (p.K != 1) continue;
+    // one-key shape: packed smallest bytes, p0, its width, the later width
+    // and the number of later positions of the word
+    uint64_t lo8 = 0;
+#pragma unroll
+    for (uint32_t pos = 0; pos < 8; ++pos) lo8 |= static_cast<uint64_t>(fl[pos] & 255u) << (56 - 8 * pos);
+    const uint32_t w0 = fl[p0 & 7] >> 16, n = split && L > p0 + 1 ? min(L, 8u) - 1 - p0 : 0u;
+    f[18] = static_cast<uint32_t>(lo8 >> 32);
+    f[19] = static_cast<uint32_t>(lo8);
+    f[20] = (p0 & 7) | (w0 << 8) | (wl << 16) | (n << 24);
   }
 }
 
@@ -1192,31 +1204,49 @@ __device__ bool maybe_prefetch(uint8_t* buf, const AutoView& v, uint32_t seg, ui
 // ---- one-key segments: byte recoding -----------------------------------
 // A one-key segment's keys (big-endian, bytes past the word zero) are recoded
 // position by position: byte position p (0 = most significant) maps value b to
-// b - lo_p in a field as wide as hi_p - lo_p needs, where lo_p and hi_p are
-// the smallest and largest byte at p in the segment, and the fields are laid
-// out most significant first.  The code orders like the key (the byte order is
-// kept within every field and the fields follow the byte positions) and
-// decodes back exactly.  Positions where all words agree take no bits, and a
-// position of letters takes 5, so codes are narrow and their top bits spread.
+// b - lo_p in a field just wide enough for the segment's range at p, and the
+// fields are laid out most significant first.  The code orders like the key
+// (the byte order is kept within every field and the fields follow the byte
+// positions) and decodes back exactly.  A segment's ranges come from its
+// bounding splitters: positions before p0 (where the splitters first differ)
+// are constant and take no bits, position p0 takes w0 bits, each of the n
+// later positions of the word wl bits (the range of all bytes inside words, 5
+// for lower-case letters), so codes are narrow and their top bits spread.
+// key - lo (lo: every position's smallest byte, packed) has no borrows, so its
+// bytes are the field values; packing byte lanes into wl-bit fields, and back,
+// takes three halving steps of masked shifts on the two 32-bit halves.
 struct ByteCode {
-  uint32_t f[8];  // position p: lo_p | offset_p << 8 | width_p << 16
+  uint64_t lo;
+  uint32_t p0, w0, wl, n;  // n wl <= 56, p0 <= 7
   __device__ __forceinline__ uint64_t encode(uint64_t key) const {
-    uint64_t code = 0;
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const uint32_t b = static_cast<uint32_t>(key >> (56 - 8 * p)) & 255u;
-      code |= static_cast<uint64_t>(b - (f[p] & 255u)) << ((f[p] >> 8) & 63u);
-    }
-    return code;
+    const uint64_t d = (key - lo) << (8 * p0);  // lane 0 (top byte): position p0
+    const uint32_t b0 = static_cast<uint32_t>(d >> 56);
+    const uint64_t t = d << 8;  // lanes 0 .. n-1: the later positions, then zeros
+    const uint32_t s1 = 8 - wl, s2 = 16 - 2 * wl;
+    uint32_t h = static_cast<uint32_t>(t >> 32), l = static_cast<uint32_t>(t);
+    h = ((h & 0xFF00FF00u) >> s1) | (h & 0x00FF00FFu);  // 16-bit groups of 2 fields
+    l = ((l & 0xFF00FF00u) >> s1) | (l & 0x00FF00FFu);
+    h = ((h & 0xFFFF0000u) >> s2) | (h & 0x0000FFFFu);  // halves of 4 fields
+    l = ((l & 0xFFFF0000u) >> s2) | (l & 0x0000FFFFu);
+    const uint64_t packed = (static_cast<uint64_t>(h) << (4 * wl)) | l;  // lanes 0..7 in 8 wl bits
+    const uint64_t tail = n ? packed >> (wl * (8 - n)) : 0ull;
+    return (static_cast<uint64_t>(b0) << (n * wl)) | tail;
   }
   __device__ __forceinline__ uint64_t decode(uint64_t code) const {
-    uint64_t key = 0;
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const uint32_t b = static_cast<uint32_t>(code >> ((f[p] >> 8) & 63u)) & ((1u << (f[p] >> 16)) - 1u);
-      key |= static_cast<uint64_t>(b + (f[p] & 255u)) << (56 - 8 * p);
-    }
-    return key;
+    const uint32_t nt = n * wl;
+    const uint32_t b0 = static_cast<uint32_t>(code >> nt);
+    const uint64_t packed = n ? (code & ((1ull << nt) - 1)) << (wl * (8 - n)) : 0ull;
+    const uint32_t s1 = 8 - wl, s2 = 16 - 2 * wl;
+    const uint32_t m4 = wl == 8 ? 0xFFFFFFFFu : (1u << (4 * wl)) - 1u;
+    const uint32_t m2 = (1u << (2 * wl)) - 1u, m1 = ((1u << wl) - 1u) * 0x00010001u;
+    uint32_t h = static_cast<uint32_t>(packed >> (4 * wl)), l = static_cast<uint32_t>(packed) & m4;
+    h = ((h << s2) & (m2 << 16)) | (h & m2);
+    l = ((l << s2) & (m2 << 16)) | (l & m2);
+    h = ((h << s1) & (m1 << 8)) | (h & m1);
+    l = ((l << s1) & (m1 << 8)) | (l & m1);
+    const uint64_t t = (static_cast<uint64_t>(h) << 32) | l;
+    const uint64_t d = (static_cast<uint64_t>(b0) << 56) | (t >> 8);
+    return (d >> (8 * p0)) + lo;
   }
 };
 
@@ -1737,8 +1767,12 @@ __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const A
                                  uint32_t* out_perm) {
   const uint32_t* sf = v.segf + static_cast<size_t>(seg) * kSegFWords;
   ByteCode bc;
-#pragma unroll
-  for (int p = 0; p < 8; ++p) bc.f[p] = __ldg(sf + p);
+  bc.lo = (static_cast<uint64_t>(__ldg(sf + 18)) << 32) | __ldg(sf + 19);
+  const uint32_t shape = __ldg(sf + 20);
+  bc.p0 = shape & 255u;
+  bc.w0 = (shape >> 8) & 255u;
+  bc.wl = (shape >> 16) & 255u;
+  bc.n = shape >> 24;
   const uint32_t kb = __ldg(sf + 16), ib = __ldg(sf + 17);
   const uint32_t ob = v.outbase[seg];
   const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);

@@ -67,8 +67,9 @@ __host__ __device__ constexpr uint32_t auto_sample_cap(uint32_t K, uint64_t cap)
       64 * 64);
 }
 // Per-segment byte code record of the sample sort: 16 position fields (lo |
-// offset << 8 | width << 16), the code width and the index width.
-constexpr uint32_t kSegFWords = 18;
+// offset << 8 | width << 16), the code width, the index width and the
+// one-key shape (packed smallest bytes, two words; p0, w0, wl, n).
+constexpr uint32_t kSegFWords = 21;
 __host__ __device__ constexpr uint64_t auto_max_segments(uint64_t cap) {
   return cap / 1024 + 2 * kBins + 1;
 }
