@@ -1330,59 +1330,155 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
   __syncthreads();
 }
 
-// Bucket pass for one-word items: the items (distinct integers below 2^bits)
-// are counted by their top kMsdBits bits in 2^kMsdBits shared counters and
-// scattered to their bucket's range; then every item of a bucket of at most
-// kMsdMaxBucket items takes its place in the bucket by counting the smaller
-// items of its bucket.  A larger bucket (copies of a frequent word share
-// their code bits) is listed and split again by the whole block: counted on
-// the kMsd2Bits bits below the highest bit in which its items differ, its
-// sub-buckets placed or listed the same way, until the list is empty.
-// Returns false, with the items untouched in registers, when a bucket holds
-// more than kMsdScratch items: then the radix passes run.  cnt holds
-// 2^kMsdBits + 2^kMsdBits / 16 words; aux holds kMsdAuxWords words.
+// Bucket pass: the items (distinct integers below 2^bits) are counted by
+// their top kMsdBits bits in 2^kMsdBits shared counters and scattered to their
+// bucket's range; then every item of a bucket of at most kMsdMaxBucket items
+// takes its place in the bucket by counting the smaller items of its bucket.
+// A larger bucket (copies of a frequent word share their code bits) is listed
+// and split again by the whole block: counted on the kMsd2Bits bits below the
+// highest bit in which its items differ, its sub-buckets placed or listed the
+// same way, until the list is empty.  Returns false, with the items untouched
+// in registers, when a bucket holds more than the planes' scratch capacity:
+// then the radix passes run.  cnt holds 2^kMsdBits + 2^kMsdBits / 16 words;
+// aux holds kMsdAuxWords words.
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
 constexpr uint32_t kMsdMaxBucket = 128;
 constexpr uint32_t kMsd2Bits = 10;
 constexpr uint32_t kMsd2Buckets = 1u << kMsd2Bits;
 // a split bucket is copied into the counter words the sub-counters leave free
-constexpr uint32_t kMsdScratch = (kMsdBuckets - kMsd2Buckets) / 2;
+constexpr uint32_t kMsdScratchWords = kMsdBuckets - kMsd2Buckets;
 // listed buckets are disjoint and larger than kMsdMaxBucket
 constexpr uint32_t kMsdList = auto_seg_cap(1) / (kMsdMaxBucket + 1) + 1;
-constexpr uint32_t kMsdAuxWords = 4 * kRxWarps + kMsdList + 1;  // warp minima and maxima, list, its size
+// warp minima and maxima (2 kRxWarps u64, then 2 kRxWarps u32), list, its size
+constexpr uint32_t kMsdAuxWords = 6 * kRxWarps + kMsdList + 1;
 // The counters, one padding word per 16, run kMsdBuckets / 16 words past the
 // counter area (into the next plane); the list lives this far into the radix
 // counter area, clear of them.
 constexpr uint32_t kMsdAuxOffset = 1024;
 
+// Item planes of the bucket pass.  One-word items (Item64): the integer
+// itself.  Two-part items (Item96): code k and index i of the integer
+// k 2^ib + i, in a u64 and a u32 plane.  bits(v, s) is the low 32 bits of
+// v >> s, width(x, y) the bit width of x ^ y.
+struct P64 {
+  using T = uint64_t;
+  uint64_t* a;
+  static constexpr uint32_t kScratch = kMsdScratchWords / 2;
+  __device__ static T of(const Item64& x) { return x.v; }
+  __device__ T ld(uint32_t p) const { return a[p]; }
+  __device__ void st(uint32_t p, const T& v) const { a[p] = v; }
+  __device__ P64 at(uint32_t p) const { return P64{a + p}; }
+  __device__ P64 scratch(uint32_t* area) const { return P64{reinterpret_cast<uint64_t*>(area)}; }
+  __device__ static bool lt(const T& x, const T& y) { return x < y; }
+  __device__ static T lowest() { return 0ull; }
+  __device__ static T highest() { return ~0ull; }
+  __device__ static T shfl_xor(const T& x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+  __device__ uint32_t bits(const T& v, uint32_t s) const { return static_cast<uint32_t>(v >> s); }
+  __device__ uint32_t width(const T& x, const T& y) const {
+    return 64u - static_cast<uint32_t>(__clzll(x ^ y));
+  }
+};
+struct P96 {
+  using T = Item96;
+  uint64_t* k;
+  uint32_t* i;
+  uint32_t ib;
+  static constexpr uint32_t kScratch = kMsdScratchWords / 3;
+  __device__ static T of(const Item96& x) { return x; }
+  __device__ T ld(uint32_t p) const { return Item96{k[p], i[p]}; }
+  __device__ void st(uint32_t p, const T& v) const {
+    k[p] = v.k;
+    i[p] = v.i;
+  }
+  __device__ P96 at(uint32_t p) const { return P96{k + p, i + p, ib}; }
+  __device__ P96 scratch(uint32_t* area) const {
+    return P96{reinterpret_cast<uint64_t*>(area), area + 2 * kScratch, ib};
+  }
+  __device__ static bool lt(const T& x, const T& y) { return x.k < y.k || (x.k == y.k && x.i < y.i); }
+  __device__ static T lowest() { return Item96{0ull, 0u}; }
+  __device__ static T highest() { return Item96{~0ull, ~0u}; }
+  __device__ static T shfl_xor(const T& x, int o) {
+    return Item96{__shfl_xor_sync(0xffffffffu, x.k, o), __shfl_xor_sync(0xffffffffu, x.i, o)};
+  }
+  __device__ uint32_t bits(const T& v, uint32_t s) const {
+    if (s >= ib) return static_cast<uint32_t>(v.k >> (s - ib));
+    return (v.i >> s) | static_cast<uint32_t>(v.k << (ib - s));
+  }
+  __device__ uint32_t width(const T& x, const T& y) const {
+    return x.k != y.k ? ib + 64u - static_cast<uint32_t>(__clzll(x.k ^ y.k))
+                      : 32u - static_cast<uint32_t>(__clz(x.i ^ y.i));
+  }
+};
+
+// Block-wide minimum and maximum of the threads' (lo, hi), through the warp
+// slots in aux; every thread gets the result.
+template <typename P>
+__device__ __forceinline__ void block_min_max(typename P::T& lo, typename P::T& hi, uint32_t* aux) {
+  using T = typename P::T;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint64_t* mk = reinterpret_cast<uint64_t*>(aux);  // 2 kRxWarps u64
+  uint32_t* mi = aux + 4 * kRxWarps;                // 2 kRxWarps u32
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T p = P::shfl_xor(lo, o), q = P::shfl_xor(hi, o);
+    lo = P::lt(p, lo) ? p : lo;
+    hi = P::lt(hi, q) ? q : hi;
+  }
+  if (lane == 0) {
+    if constexpr (sizeof(T) == sizeof(uint64_t)) {
+      mk[warp] = lo;
+      mk[kRxWarps + warp] = hi;
+    } else {
+      mk[warp] = lo.k;
+      mk[kRxWarps + warp] = hi.k;
+      mi[warp] = lo.i;
+      mi[kRxWarps + warp] = hi.i;
+    }
+  }
+  __syncthreads();
+  if constexpr (sizeof(T) == sizeof(uint64_t)) {
+    lo = lane < kRxWarps ? mk[lane] : P::highest();
+    hi = lane < kRxWarps ? mk[kRxWarps + lane] : P::lowest();
+  } else {
+    lo = lane < kRxWarps ? Item96{mk[lane], mi[lane]} : P::highest();
+    hi = lane < kRxWarps ? Item96{mk[kRxWarps + lane], mi[kRxWarps + lane]} : P::lowest();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T p = P::shfl_xor(lo, o), q = P::shfl_xor(hi, o);
+    lo = P::lt(p, lo) ? p : lo;
+    hi = P::lt(hi, q) ? q : hi;
+  }
+}
+
 // Puts every item of a[0..m) at its place within its bucket.  The items lie
-// bucket by bucket (bucket d = digit(item) ends at cnt[d]).  Thread t takes
-// positions t, t + kSegThreads, ... (a warp: 32 neighbours, mostly of a few
-// buckets, whose items it reads as broadcasts), counts the smaller items of
-// the bucket and, after a barrier, stores its item at the bucket's start plus
-// that count.  Bucket d's end is cnt[slot(d)].  A bucket of more than kMsdMaxBucket items stays in place and is
-// appended to list as (base0 + start) | size << 16 by the thread holding its
-// first item.
-template <int E, typename Digit, typename Slot>
-__device__ __forceinline__ void rank_buckets(uint64_t* a, uint32_t m, const uint32_t* cnt, Digit digit,
+// bucket by bucket; bucket d = digit(item) ends at cnt[slot(d)].  Thread t
+// takes positions t, t + kSegThreads, ... (a warp: 32 neighbours, mostly of a
+// few buckets, whose items it reads as broadcasts), counts the smaller items
+// of the bucket and, after a barrier, stores its item at the bucket's start
+// plus that count.  A bucket of more than kMsdMaxBucket items stays in place
+// and is appended to list as (base0 + start) | size << 16 by the thread
+// holding its first item.
+template <int E, typename P, typename Digit, typename Slot>
+__device__ __forceinline__ void rank_buckets(const P& a, uint32_t m, const uint32_t* cnt, Digit digit,
                                              Slot slot, uint32_t base0, uint32_t* list, uint32_t* n_list) {
-  uint64_t v[E];
+  typename P::T v[E];
   uint32_t dst[E];
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     const uint32_t i = threadIdx.x + k * kSegThreads;
-    v[k] = 0;
+    v[k] = P::lowest();
     dst[k] = ~0u;
     if (i < m) {
-      v[k] = a[i];
+      v[k] = a.ld(i);
       const uint32_t d = digit(v[k]);
       const uint32_t lo = d ? cnt[slot(d - 1)] : 0u, hi = cnt[slot(d)];
       if (hi - lo > kMsdMaxBucket) {
         if (i == lo) list[atomicAdd(n_list, 1u)] = (base0 + lo) | ((hi - lo) << 16);
       } else if (hi - lo > 1) {
         uint32_t r = lo;
-        for (uint32_t q = lo; q < hi; ++q) r += a[q] < v[k] ? 1u : 0u;
+        for (uint32_t q = lo; q < hi; ++q) r += P::lt(a.ld(q), v[k]) ? 1u : 0u;
         dst[k] = r;
       }
     }
@@ -1390,21 +1486,22 @@ __device__ __forceinline__ void rank_buckets(uint64_t* a, uint32_t m, const uint
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < E; ++k)
-    if (dst[k] != ~0u) a[dst[k]] = v[k];
+    if (dst[k] != ~0u) a.st(dst[k], v[k]);
 }
 
 // Splits the listed buckets until none is left (the list is read after a
 // barrier).  The counter area holds the copy of the bucket being split
-// (kMsdScratch items) and its kMsd2Buckets sub-counters.  The items of a
+// (P::kScratch items) and its kMsd2Buckets sub-counters.  The items of a
 // bucket are distinct: its minimum and maximum differ, the kMsd2Bits window
 // ending at their highest differing bit holds at least two digits, and every
 // sub-bucket shares one more bit than its parent, so the splitting ends.
-__device__ __forceinline__ void split_buckets(uint64_t* a, uint32_t* area, uint32_t* aux,
+template <typename P>
+__device__ __forceinline__ void split_buckets(const P& a, uint32_t* area, uint32_t* aux,
                                               uint32_t* warp_tmp) {
-  uint64_t* scratch = reinterpret_cast<uint64_t*>(area);
-  uint32_t* sub = area + 2 * kMsdScratch;
-  uint64_t* mm = reinterpret_cast<uint64_t*>(aux);  // warp minima, then maxima
-  uint32_t* list = aux + 4 * kRxWarps;
+  using T = typename P::T;
+  const P scratch = a.scratch(area);
+  uint32_t* sub = area + kMsdScratchWords;
+  uint32_t* list = aux + 6 * kRxWarps;
   uint32_t* n_list = list + kMsdList;
   constexpr uint32_t per = kMsd2Buckets / kSegThreads;  // sub-counters per thread
   static_assert(per * kSegThreads == kMsd2Buckets, "sub-counters split evenly over the threads");
@@ -1416,38 +1513,20 @@ __device__ __forceinline__ void split_buckets(uint64_t* a, uint32_t* area, uint3
     const uint32_t lo = e & 0xFFFFu, m = e >> 16;
     __syncthreads();  // the entry is read before it is replaced
     if (threadIdx.x == 0) *n_list = t - 1;
-    uint64_t vmin = ~0ull, vmax = 0;
+    T vmin = P::highest(), vmax = P::lowest();
     for (uint32_t i = threadIdx.x; i < m; i += kSegThreads) {
-      const uint64_t y = a[lo + i];
-      scratch[i] = y;
-      vmin = y < vmin ? y : vmin;
-      vmax = y > vmax ? y : vmax;
+      const T y = a.ld(lo + i);
+      scratch.st(i, y);
+      vmin = P::lt(y, vmin) ? y : vmin;
+      vmax = P::lt(vmax, y) ? y : vmax;
     }
 #pragma unroll
     for (uint32_t k = 0; k < per; ++k) sub[threadIdx.x * per + k] = 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t p = __shfl_xor_sync(0xffffffffu, vmin, o), q = __shfl_xor_sync(0xffffffffu, vmax, o);
-      vmin = p < vmin ? p : vmin;
-      vmax = q > vmax ? q : vmax;
-    }
-    if (lane == 0) {
-      mm[warp] = vmin;
-      mm[kRxWarps + warp] = vmax;
-    }
-    __syncthreads();
-    vmin = lane < kRxWarps ? mm[lane] : ~0ull;
-    vmax = lane < kRxWarps ? mm[kRxWarps + lane] : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t p = __shfl_xor_sync(0xffffffffu, vmin, o), q = __shfl_xor_sync(0xffffffffu, vmax, o);
-      vmin = p < vmin ? p : vmin;
-      vmax = q > vmax ? q : vmax;
-    }
-    const uint32_t hb = 64u - static_cast<uint32_t>(__clzll(vmin ^ vmax));
+    block_min_max<P>(vmin, vmax, aux);
+    const uint32_t hb = a.width(vmin, vmax);
     const uint32_t sh = hb > kMsd2Bits ? hb - kMsd2Bits : 0u;
     for (uint32_t i = threadIdx.x; i < m; i += kSegThreads)
-      atomicAdd(&sub[static_cast<uint32_t>(scratch[i] >> sh) & (kMsd2Buckets - 1)], 1u);
+      atomicAdd(&sub[a.bits(scratch.ld(i), sh) & (kMsd2Buckets - 1)], 1u);
     __syncthreads();
     uint32_t c[per], sum = 0;
 #pragma unroll
@@ -1468,21 +1547,20 @@ __device__ __forceinline__ void split_buckets(uint64_t* a, uint32_t* area, uint3
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < m; i += kSegThreads) {
-      const uint64_t y = scratch[i];
-      a[lo + atomicAdd(&sub[static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1)], 1u)] = y;
+      const T y = scratch.ld(i);
+      a.st(lo + atomicAdd(&sub[a.bits(y, sh) & (kMsd2Buckets - 1)], 1u), y);
     }
     __syncthreads();
-    rank_buckets<(kMsdScratch + kSegThreads - 1) / kSegThreads>(
-        a + lo, m, sub, [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh) & (kMsd2Buckets - 1); },
+    rank_buckets<(P::kScratch + kSegThreads - 1) / kSegThreads>(
+        a.at(lo), m, sub, [a, sh](const T& y) { return a.bits(y, sh) & (kMsd2Buckets - 1); },
         [](uint32_t d) { return d; }, lo, list, n_list);
     __syncthreads();
   }
 }
 
-template <int E>
-__device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t nv, uint32_t bits,
-                                                  uint64_t* a, uint32_t* cnt, uint32_t* warp_tmp,
-                                                  uint32_t* aux) {
+template <int E, typename P, typename It>
+__device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv, uint32_t bits, const P& a,
+                                                  uint32_t* cnt, uint32_t* warp_tmp, uint32_t* aux) {
   const uint32_t sh = bits > kMsdBits ? bits - kMsdBits : 0u;
   constexpr uint32_t per = kMsdBuckets / kSegThreads;  // counters per thread
   static_assert(per == 16 && per * kSegThreads == kMsdBuckets, "16 counters per thread");
@@ -1495,7 +1573,7 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) atomicAdd(&cnt[slot(static_cast<uint32_t>(x[j].v >> sh))], 1u);
+    if (j < nv) atomicAdd(&cnt[slot(a.bits(P::of(x[j]), sh))], 1u);
   __syncthreads();
   // exclusive scan of the counts (thread t owns counters t*per .. t*per+per-1)
   uint32_t v[per], sum = 0, mx = 0;
@@ -1517,24 +1595,24 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
   uint32_t tm = lane < kRxWarps ? warp_tmp[kRxWarps + lane] : 0u;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tm = max(tm, __shfl_xor_sync(0xffffffffu, tm, o));
-  if (tm > kMsdScratch) return false;  // block-uniform
+  if (tm > P::kScratch) return false;  // block-uniform
   uint32_t run = __shfl_sync(0xffffffffu, tupto - tw, warp) + inc - sum;
 #pragma unroll
   for (uint32_t k = 0; k < per; ++k) {
     mine[k] = run;  // bucket start, then its cursor
     run += v[k];
   }
-  uint32_t* n_list = aux + 4 * kRxWarps + kMsdList;
+  uint32_t* list = aux + 6 * kRxWarps;
+  uint32_t* n_list = list + kMsdList;
   if (threadIdx.x == 0) *n_list = 0;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) a[atomicAdd(&cnt[slot(static_cast<uint32_t>(x[j].v >> sh))], 1u)] = x[j].v;
+    if (j < nv) a.st(atomicAdd(&cnt[slot(a.bits(P::of(x[j]), sh))], 1u), P::of(x[j]));
   __syncthreads();
   // cnt[slot(b)] is now the end of bucket b; bucket b spans [end(b-1), end(b))
   rank_buckets<E>(a, cnt[slot(kMsdBuckets - 1)], cnt,
-                  [sh](uint64_t y) { return static_cast<uint32_t>(y >> sh); }, slot, 0u, aux + 4 * kRxWarps,
-                  n_list);
+                  [a, sh](const typename P::T& y) { return a.bits(y, sh); }, slot, 0u, list, n_list);
   __syncthreads();
   if (tm > kMsdMaxBucket) split_buckets(a, cnt, aux, warp_tmp);  // block-uniform
   return true;
@@ -1546,11 +1624,12 @@ __device__ __forceinline__ bool bucket_sort_items(const Item64 (&x)[E], uint32_t
 // items of a warp in position order (running per-warp digit counters
 // hist[w][*] plus the lanes below with the same digit), scans the counters,
 // and scatters every item to its new position in the store.  The sorted items
-// end in st[0, c).
-template <typename It, typename St, int E, typename Get>
-__device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t bits, uint32_t ib,
+// end in st[0, c).  With bucket counters given, the bucket pass is tried
+// first; when it succeeds (the return value) the items end in bp[0, c).
+template <typename It, typename St, int E, typename Get, typename BP>
+__device__ __forceinline__ bool radix_sort_items(Get get, uint32_t c, uint32_t bits, uint32_t ib,
                                                  St st, uint16_t* hist, uint32_t* warp_tmp,
-                                                 uint32_t* bucket_cnt) {
+                                                 uint32_t* bucket_cnt, const BP& bp) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t S = ((c + kRxWarps - 1) / kRxWarps + 31) & ~31u;
   const uint32_t w0 = warp * S, p0 = w0 + lane, lt = lanemask_lt();
@@ -1565,12 +1644,10 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
   // every item is read before the first pass scatters into the store
   __syncthreads();
   // byte-recoded keys spread their top bits: the bucket pass is tried first
-  if constexpr (sizeof(It) == sizeof(Item64)) {
-    if (bucket_cnt && bits > 8 &&
-        bucket_sort_items<E>(x, nv, bits, st.a, bucket_cnt, warp_tmp,
-                             reinterpret_cast<uint32_t*>(hist) + kMsdAuxOffset))
-      return;
-  }
+  if (bucket_cnt && bits > 8 &&
+      bucket_sort_items<E>(x, nv, bits, bp, bucket_cnt, warp_tmp,
+                           reinterpret_cast<uint32_t*>(hist) + kMsdAuxOffset))
+    return true;
   uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
   for (uint32_t s = 0; s < bits; s += 8) {
     for (uint32_t i = lane; i < kRxDigits; i += 32) row[i] = 0;
@@ -1611,6 +1688,7 @@ __device__ __forceinline__ void radix_sort_items(Get get, uint32_t c, uint32_t b
         if (j < nv) x[j] = st.load(p0 + 32 * j);
     }
   }
+  return false;
 }
 
 // Sorts the segment's items (converted from the key and index planes, which
@@ -1631,7 +1709,7 @@ __device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, ByteCode bc,
   if constexpr (sizeof(It) == sizeof(Item64)) {
     auto get = [=](uint32_t p) { return Item64{(bc.encode(kp[p]) << ib) | ip[p]}; };
     // the index plane is free once the items are in registers: bucket counters
-    radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp, ip);
+    radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp, ip, P64{kp});
     const uint64_t imask = (1ull << ib) - 1;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       const uint64_t v = kp[r];
@@ -1642,11 +1720,17 @@ __device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, ByteCode bc,
     }
   } else {
     auto get = [=](uint32_t p) { return Item96{bc.encode(kp[p]), ip[p]}; };
-    radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp, nullptr);
+    // up to half the capacity, the bucket pass keeps the codes in the key
+    // plane and the indices in its upper half, the counters in the index plane
+    constexpr uint32_t H = C / 2;
+    const P96 bp{kp, reinterpret_cast<uint32_t*>(kp + H), ib};
+    const bool bucketed = radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp,
+                                                           c <= H ? ip : nullptr, bp);
+    const uint32_t* op = bucketed ? bp.i : ip;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       Elem<1> e;
       e.k[0] = bc.decode(kp[r]);
-      e.idx = ip[r];
+      e.idx = op[r];
       write_word<1>(W, out_rec, out_perm, ob + r, e);
     }
   }
@@ -1712,7 +1796,7 @@ __device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32
   if constexpr (sizeof(It) == sizeof(Item64)) {
     auto get = [=](uint32_t p) { return Item64{(encode16(f, k0p[p], k1p[p]) << ib) | ip[p]}; };
     radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{k0p}, hist, warp_tmp,
-                                     reinterpret_cast<uint32_t*>(k1p));
+                                     reinterpret_cast<uint32_t*>(k1p), P64{k0p});
     const uint64_t imask = (1ull << ib) - 1;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       const uint64_t v = k0p[r];
@@ -1723,11 +1807,16 @@ __device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32
     }
   } else {
     auto get = [=](uint32_t p) { return Item96{encode16(f, k0p[p], k1p[p]), ip[p]}; };
-    radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{k0p, ip}, hist, warp_tmp, nullptr);
+    // the bucket pass keeps the codes in plane 0 and the indices in the lower
+    // half of plane 1; its counters take the upper half and the index plane
+    const P96 bp{k0p, reinterpret_cast<uint32_t*>(k1p), ib};
+    const bool bucketed = radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{k0p, ip}, hist, warp_tmp,
+                                                           reinterpret_cast<uint32_t*>(k1p + C / 2), bp);
+    const uint32_t* op = bucketed ? bp.i : ip;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       Elem<2> e;
       decode16(f, k0p[r], e);
-      e.idx = ip[r];
+      e.idx = op[r];
       write_word<2>(W, out_rec, out_perm, ob + r, e);
     }
   }
@@ -1952,12 +2041,20 @@ static_assert(auto_seg_cap(2) <= 8 * kSegThreads, "eight radix items per thread 
 static_assert(kMsdBuckets <= auto_seg_cap(1), "bucket counters fit the index plane");
 static_assert((kMsdAuxOffset + kMsdAuxWords) * 4 <= kRxWarps * kRxDigits * sizeof(uint16_t),
               "split list fits the radix counters");
+// two-part items: one-key segments keep their indices in the upper half of
+// the key plane (segments of at most half the capacity), two-key segments in
+// the lower half of key plane 1, whose upper half and the index plane hold the
+// counters
+static_assert(auto_seg_cap(1) / 2 * 12 <= auto_seg_cap(1) * 8 && auto_seg_cap(2) * 4 <= auto_seg_cap(2) / 2 * 8 &&
+                  auto_seg_cap(2) / 2 * 8 + auto_seg_cap(2) * 4 >= kMsdBuckets * 4,
+              "two-part item planes and counters fit the segment planes");
 // one-key segments: counters in the index plane and the first kMsdBuckets / 16
 // words of the radix counters; two-key segments: in key plane 1 and the first
 // words of the index plane
 static_assert(kMsdBuckets / 16 <= kMsdAuxOffset && kMsdBuckets / 16 <= auto_seg_cap(2),
               "padded bucket counters stay clear of the split list");
-static_assert(2 * kMsdScratch + kMsd2Buckets <= kMsdBuckets && kMsdScratch < 65536 && auto_seg_cap(1) <= 65536,
+static_assert(2 * P64::kScratch + kMsd2Buckets <= kMsdBuckets && 3 * P96::kScratch + kMsd2Buckets <= kMsdBuckets &&
+                  auto_seg_cap(1) < 65536,
               "split copy and sub-counters fit the counter area; list entries pack start and size");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
 // a few scalars; ptxas -v reports it) + 1 KB reserved each

@@ -17,6 +17,7 @@ from paper_1411_5283_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 M64 = (1 << 64) - 1
+MIXED = bytes(range(ord("A"), ord("Z") + 1)) + bytes(range(ord("a"), ord("z") + 1))
 
 
 @pytest.fixture(scope="module")
@@ -129,35 +130,39 @@ def test_auto_frequent_words_split_their_buckets(env):
     assert_same_answer(out_rec, out_perm, off, expect, n)
 
 
-def test_auto_frequent_word_missed_by_sample_overfills_a_bucket(env):
+@pytest.mark.parametrize("L,alphabet", [(4, b"abcdefghijklmnopqrstuvwxyz"), (8, MIXED)])
+def test_auto_frequent_word_missed_by_sample_overfills_a_bucket(env, L, alphabet):
     """4,000 copies of one word, all at positions the stratified sample skips,
     among random words: the segment that receives them stays resident but one
     bucket of the first counting pass holds more items than the split copy
-    area, so the segment takes the radix passes."""
+    area, so the segment takes the radix passes (one-word items for four
+    lower-case letters, two-part items for eight mixed-case ones)."""
     torch, bs, orc = env
     n, W = 120_000, 8
     rng = np.random.default_rng(5)
     rec = np.zeros((n, W), np.uint8)
-    rec[:, :4] = rng.integers(ord("a"), ord("z") + 1, size=(n, 4), dtype=np.uint8)
+    a = np.frombuffer(alphabet, np.uint8)
+    rec[:, :L] = a[rng.integers(0, a.size, size=(n, L))]
     sampled = np.zeros(n, bool)
     for s in range((n + 31) // 32):
         i = s * 32 + (_mix64((s + 0x9E3779B97F4A7C15) & M64) & 31)
         if i < n:
             sampled[i] = True
     free = np.flatnonzero(~sampled)
-    rec[rng.choice(free, 4000, replace=False), :4] = np.frombuffer(b"mmmm", np.uint8)
-    ln = np.full(n, 4, np.uint8)
+    rec[rng.choice(free, 4000, replace=False), :L] = ord("m")
+    ln = np.full(n, L, np.uint8)
     expect = orc.stable_sort(orc.Words(rec, ln))
     s, (out_rec, out_perm, off) = run(env, rec, ln)
     assert s.status() == 0
     assert_same_answer(out_rec, out_perm, off, expect, n)
 
 
-@pytest.mark.parametrize("alphabet", [bytes(range(256)), b"q", b"pq"])
+@pytest.mark.parametrize("alphabet", [bytes(range(256)), b"q", b"pq", MIXED])
 def test_auto_byte_ranges(env, alphabet):
     """Segment byte codes follow from the splitters and the range of all bytes
     inside words: every byte value (fields of 8 bits, codes too wide for one
-    machine word), a single letter (every field empty) and two letters."""
+    machine word), a single letter (every field empty), two letters, and
+    mixed-case letters (6-bit fields: two-part items from seven letters on)."""
     torch, bs, orc = env
     n, W = 200_000, 16
     rec, ln = table(23, n, W, alphabet)
