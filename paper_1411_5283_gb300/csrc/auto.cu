@@ -164,6 +164,34 @@ __device__ void bucket_geometry(uint32_t cnt, uint32_t K, uint32_t* g, uint32_t*
 // (dir[b] = splitters whose first byte is below b), then K key planes and the
 // index plane of its g - 1 splitters.
 constexpr uint32_t kDirBytes = kAutoDirBytes;
+static_assert(kDirBytes >= 2 * (kAutoDir2Max + 1) && kDirBytes >= 2 * 257 && kDirBytes % 16 == 0,
+              "the directory area holds either directory, 16-byte aligned");
+
+// Directory code of a first key word.  Bytes fall into r classes: 0 below
+// band (a word's zero tail), 1 .. r-1 for band .. bor (and above, only in the
+// all-ones splitters of an unsampled bucket).  When r^2 <= kAutoDir2Max the
+// code is the class pair of the first two bytes, c0 r + c1, else the first
+// byte; either way it never decreases as the key grows, so a bucket's sorted
+// splitters have sorted codes, and a splitter whose code differs from an
+// element's compares with it as the codes do.
+struct DirShape {
+  uint32_t band, r;
+  bool two;
+};
+__device__ __forceinline__ DirShape dir_shape(const AutoHdr* h) {
+  const uint32_t band = h->band, bor = h->bor;
+  const uint32_t r = bor >= band ? bor - band + 2 : 2u;
+  return DirShape{band, r, r * r <= kAutoDir2Max};
+}
+__device__ __forceinline__ uint32_t dir_class(uint32_t b, const DirShape& d) {
+  return b < d.band ? 0u : min(b - d.band + 1, d.r - 1);
+}
+__device__ __forceinline__ uint32_t dir_code(uint64_t k0, const DirShape& d) {
+  const uint32_t b0 = static_cast<uint32_t>(k0 >> 56);
+  if (!d.two) return b0;
+  return dir_class(b0, d) * d.r + dir_class(static_cast<uint32_t>(k0 >> 48) & 255u, d);
+}
+__device__ __forceinline__ uint32_t dir_entries(const DirShape& d) { return d.two ? d.r * d.r : 256u; }
 
 __device__ __forceinline__ uint32_t spl_bytes_of(uint32_t g, uint32_t K) {
   return g >= 2 ? static_cast<uint32_t>(kDirBytes + align_up((g - 1) * (8 * K + 4), 16)) : 0u;
@@ -680,9 +708,9 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
 }
 
 // (c) grid (W, kSplDirCtas): the CTAs of bucket L write its segments' byte
-// code records; CTA (L-1, 0) also the directory dir[b] = number of splitters
-// whose first byte is below b (splitters are sorted, so their first bytes
-// never decrease).
+// code records and its directory: dir[c] = number of splitters whose
+// directory code is below c (splitters are sorted, so their codes never
+// decrease).
 constexpr uint32_t kSplDirCtas = 4;
 __global__ void __launch_bounds__(288)
 auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
@@ -695,18 +723,21 @@ auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoV
   if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
   __syncthreads();
   if (p.K <= 2) segment_codes(v, p, L);
-  if (p.g < 2 || blockIdx.y > 0) return;
-  const uint32_t ns = p.g - 1, b = threadIdx.x;
-  if (b > 256) return;
+  if (p.g < 2) return;
+  const uint32_t ns = p.g - 1;
+  const DirShape ds = dir_shape(v.hdr);
+  const uint32_t N = dir_entries(ds);
   uint16_t* dir = reinterpret_cast<uint16_t*>(v.spl + p.spl_off);
   const uint64_t* sk0 = reinterpret_cast<const uint64_t*>(v.spl + p.spl_off + kDirBytes);
-  uint32_t lo = 0, hi = ns;  // first splitter with first byte >= b
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if ((sk0[mid] >> 56) < b) lo = mid + 1;
-    else hi = mid;
+  for (uint32_t c = blockIdx.y * blockDim.x + threadIdx.x; c <= N; c += gridDim.y * blockDim.x) {
+    uint32_t lo = 0, hi = ns;  // first splitter with code >= c
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (dir_code(sk0[mid], ds) < c) lo = mid + 1;
+      else hi = mid;
+    }
+    dir[c] = static_cast<uint16_t>(lo);
   }
-  dir[b] = static_cast<uint16_t>(lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -718,57 +749,6 @@ struct __align__(16) PartPlan {
   uint32_t g, seg0, spl_off, cap;
   uint64_t r64, r32;
 };
-
-// Segment (index within the bucket) of an element with K key words, first
-// key word k0 and input index i, in a bucket whose splitter table (directory,
-// key planes, indices) starts at tab and holds g - 1 splitters: the number of
-// splitters <= the element.  key(k) reads key word k >= 1, needed only when
-// the first words tie.  The first-byte directory narrows the search to
-// [lo, hi]; every lane of the warp takes the same number of halving steps
-// (the warp's largest range), so the loop does not diverge.  All lanes call;
-// a lane with active == false gets 0.
-template <typename KeyK>
-__device__ __forceinline__ uint32_t find_segment(const uint8_t* tab, uint32_t g, uint32_t K,
-                                                 uint64_t k0, uint32_t i, bool active, KeyK key) {
-  const uint32_t ns = g - 1;
-  const uint16_t* dir = reinterpret_cast<const uint16_t*>(tab);
-  const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + kDirBytes);
-  const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(K) * ns);
-  // splitters below dir[c] have a smaller first byte (all <= the element),
-  // those from dir[c+1] on a larger one
-  const uint32_t c = static_cast<uint32_t>(k0 >> 56);
-  uint32_t lo = 0, hi = 0;
-  if (active) {
-    lo = dir[c];
-    hi = dir[c + 1];
-  }
-  const uint32_t steps = __reduce_max_sync(0xffffffffu, 32u - __clz(hi - lo));
-  for (uint32_t t = 0; t < steps; ++t) {
-    if (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1, sp = mid - 1;  // is splitter mid-1 <= element ?
-      const uint64_t a = sk[sp];
-      bool le = a < k0;
-      if (a == k0) {
-        if (K == 1) {
-          le = si[sp] <= i;
-        } else {
-          // multi-key tie on the first word (rare): later words, then the index
-          uint32_t k = 1;
-          uint64_t ak = 0, bk = 0;
-          for (; k < K; ++k) {
-            ak = sk[k * ns + sp];
-            bk = key(k);
-            if (ak != bk) break;
-          }
-          le = k < K ? ak < bk : si[sp] <= i;
-        }
-      }
-      lo = le ? mid : lo;
-      hi = le ? hi : mid - 1;
-    }
-  }
-  return lo;
-}
 
 // ---- 3a. length buckets -------------------------------------------------
 // Tiles of kBucketTile words: each tile counts its words per length in shared
@@ -881,6 +861,66 @@ constexpr uint32_t kPartCounters = 8192;                  // segments per bucket
 constexpr uint32_t kPartSplSmem = 72 * 1024;              // bucket splitter table staged up to this size
 constexpr size_t kPartSmem = kPartCounters * 4 + kPartSplSmem;
 
+// Segments (indices within the bucket) of a thread's kPartPer elements (first
+// key words k0, input indices i; active[u] false for none), in a bucket whose
+// splitter table (directory, key planes, indices) starts at tab and holds g - 1
+// splitters: the number of splitters <= the element.  key(u, k) reads key word
+// k >= 1 of element u, needed only when first words tie.  The directory
+// narrows each search to the splitters with the element's directory code,
+// [lo, hi]; the searches step together (one halving step of every element per
+// round, their loads independent) for as many rounds as the warp's widest
+// range needs, so the loop does not diverge.
+template <typename KeyK>
+__device__ __forceinline__ void find_segments(const uint8_t* tab, const DirShape& ds, uint32_t g, uint32_t K,
+                                              const uint64_t (&k0)[kPartPer], const uint32_t (&i)[kPartPer],
+                                              const bool (&active)[kPartPer], KeyK key,
+                                              uint32_t (&seg)[kPartPer]) {
+  const uint32_t ns = g - 1;
+  const uint16_t* dir = reinterpret_cast<const uint16_t*>(tab);
+  const uint64_t* sk = reinterpret_cast<const uint64_t*>(tab + kDirBytes);
+  const uint32_t* si = reinterpret_cast<const uint32_t*>(sk + static_cast<size_t>(K) * ns);
+  // splitters below dir[c] have a smaller code (all <= the element), those
+  // from dir[c+1] on a larger one
+  uint32_t lo[kPartPer], hi[kPartPer], w = 0;
+#pragma unroll
+  for (uint32_t u = 0; u < kPartPer; ++u) {
+    const uint32_t c = dir_code(k0[u], ds);
+    lo[u] = active[u] ? dir[c] : 0u;
+    hi[u] = active[u] ? dir[c + 1] : 0u;
+    w = max(w, 32u - static_cast<uint32_t>(__clz(hi[u] - lo[u])));
+  }
+  const uint32_t steps = __reduce_max_sync(0xffffffffu, w);
+  for (uint32_t t = 0; t < steps; ++t) {
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+      if (lo[u] < hi[u]) {
+        const uint32_t mid = (lo[u] + hi[u] + 1) >> 1, sp = mid - 1;  // is splitter mid-1 <= element ?
+        const uint64_t a = sk[sp];
+        bool le = a < k0[u];
+        if (a == k0[u]) {
+          if (K == 1) {
+            le = si[sp] <= i[u];
+          } else {
+            // multi-key tie on the first word (rare): later words, then the index
+            uint32_t k = 1;
+            uint64_t ak = 0, bk = 0;
+            for (; k < K; ++k) {
+              ak = sk[k * ns + sp];
+              bk = key(u, k);
+              if (ak != bk) break;
+            }
+            le = k < K ? ak < bk : si[sp] <= i[u];
+          }
+        }
+        lo[u] = le ? mid : lo[u];
+        hi[u] = le ? hi[u] : mid - 1;
+      }
+    }
+  }
+#pragma unroll
+  for (uint32_t u = 0; u < kPartPer; ++u) seg[u] = lo[u];
+}
+
 __global__ void __launch_bounds__(kPartThreads2, 2)
 auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_pass, Ws ws,
                       AutoView av) {
@@ -907,11 +947,12 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
   }
   __syncthreads();
   const uint32_t tiles = tp[W + 1];
+  const DirShape ds = dir_shape(v.hdr);
   uint32_t staged = 0;  // bucket whose splitter table is in shared memory
   bool overflow = false;
+  uint32_t L = 1;  // bucket of tile t (block-uniform; a CTA's tiles increase)
   for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    uint32_t L = 1;
-    while (L < W && tp[L + 1] <= t) ++L;  // block-uniform
+    while (L < W && tp[L + 1] <= t) ++L;
     const PartPlan p = plans[L];
     const uint32_t K = keys_for_len(L), count = s_off[L + 1] - s_off[L];
     const uint32_t e0 = (t - tp[L]) * kPartTile, m = min(kPartTile, count - e0);
@@ -922,7 +963,8 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
     const uint32_t tb = p.g > 1 ? static_cast<uint32_t>(spl_bytes_of(p.g, K)) : 0u;
     const bool tab_smem = tb <= kPartSplSmem;
     if (tab_smem && tb && staged != L) {
-      __syncthreads();  // earlier readers of the staged table are done
+      // earlier readers of the staged table are done (barrier ending the
+      // previous tile)
       const uint4* src = reinterpret_cast<const uint4*>(tab);
       uint4* dst = reinterpret_cast<uint4*>(tabs);
       for (uint32_t q = threadIdx.x; q < tb / 16; q += blockDim.x) dst[q] = src[q];
@@ -932,45 +974,53 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
     const bool local = p.g <= kPartCounters;
     if (local)
       for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) cnt[q] = 0;
-    __syncthreads();
-    // segment (within the bucket) and slot of every element: s << 16 | slot
-    uint32_t sr[kPartPer], idxs[kPartPer];
+    uint32_t idxs[kPartPer];
     uint64_t key0s[kPartPer];
+    bool in[kPartPer];
 #pragma unroll
     for (uint32_t q = 0; q < kPartPer; ++q) {
       const uint32_t e = q * kPartThreads2 + threadIdx.x;
-      key0s[q] = e < m ? k0p[e0 + e] : 0ull;
-      idxs[q] = e < m ? ipp[e0 + e] : 0u;
+      in[q] = e < m;
+      key0s[q] = in[q] ? k0p[e0 + e] : 0ull;
+      idxs[q] = in[q] ? ipp[e0 + e] : 0u;
+    }
+    __syncthreads();  // table and zeroed counters visible
+    // segment (within the bucket) and slot of every element: s << 16 | slot
+    uint32_t sg[kPartPer], sr[kPartPer];
+    const auto keyk = [&](uint32_t u, uint32_t k) {
+      return k0p[static_cast<uint64_t>(k) * count + e0 + u * kPartThreads2 + threadIdx.x];
+    };
+    if (p.g > 1) {
+      find_segments(tab, ds, p.g, K, key0s, idxs, in, keyk, sg);
+    } else {
+#pragma unroll
+      for (uint32_t q = 0; q < kPartPer; ++q) sg[q] = 0;
     }
 #pragma unroll
     for (uint32_t q = 0; q < kPartPer; ++q) {
       const uint32_t e = q * kPartThreads2 + threadIdx.x;
-      const bool in = e < m;
-      const uint64_t key0 = key0s[q];
-      const uint32_t idx = idxs[q];
-      auto keyk = [&](uint32_t k) { return k0p[static_cast<uint64_t>(k) * count + e0 + e]; };
-      const uint32_t sg = p.g > 1 ? find_segment(tab, p.g, K, key0, idx, in, keyk) : 0u;
       uint32_t slot = 0;
-      if (in) slot = local ? atomicAdd(&cnt[sg], 1u) : atomicAdd(&v.cursor[(p.seg0 + sg) * kCursorStride], 1u);
-      sr[q] = (in && local) ? (sg << 16 | slot) : 0xFFFFFFFFu;
-      if (!local && in) {
+      if (in[q]) slot = local ? atomicAdd(&cnt[sg[q]], 1u) : atomicAdd(&v.cursor[(p.seg0 + sg[q]) * kCursorStride], 1u);
+      sr[q] = (in[q] && local) ? (sg[q] << 16 | slot) : 0xFFFFFFFFu;
+      if (!local && in[q]) {
         // no tile counting: the slot came from the segment's cursor directly
         const uint32_t pos = slot;
         uint32_t rc;
         uint64_t rb, ib;
         if (!retry_pass) {
           rc = p.cap;
-          rb = p.r64 + static_cast<uint64_t>(sg) * p.cap * K;
-          ib = p.r32 + static_cast<uint64_t>(sg) * p.cap;
+          rb = p.r64 + static_cast<uint64_t>(sg[q]) * p.cap * K;
+          ib = p.r32 + static_cast<uint64_t>(sg[q]) * p.cap;
         } else {
-          rc = v.rcap[p.seg0 + sg];
-          rb = v.rbase[p.seg0 + sg];
-          ib = v.ibase[p.seg0 + sg];
+          rc = v.rcap[p.seg0 + sg[q]];
+          rb = v.rbase[p.seg0 + sg[q]];
+          ib = v.ibase[p.seg0 + sg[q]];
         }
         if (pos < rc) {
-          for (uint32_t k = 0; k < K; ++k)
+          v.area64[rb + pos] = key0s[q];
+          for (uint32_t k = 1; k < K; ++k)
             v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = k0p[static_cast<uint64_t>(k) * count + e0 + e];
-          v.area32[ib + pos] = idx;
+          v.area32[ib + pos] = idxs[q];
         } else {
           overflow = true;
         }
@@ -981,35 +1031,39 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
       // one run per segment the tile touches; the reservations of a thread
       // are issued back to back
       constexpr uint32_t per = kPartCounters / kPartThreads2;
+      const uint32_t rounds = (p.g + kPartThreads2 - 1) / kPartThreads2;  // block-uniform, <= per
       uint32_t got[per];
 #pragma unroll
       for (uint32_t k = 0; k < per; ++k) {
+        if (k >= rounds) break;
         const uint32_t q = k * kPartThreads2 + threadIdx.x;
         const uint32_t c = q < p.g ? cnt[q] : 0u;
         got[k] = c ? atomicAdd(&v.cursor[(p.seg0 + q) * kCursorStride], c) : 0u;
       }
 #pragma unroll
       for (uint32_t k = 0; k < per; ++k) {
+        if (k >= rounds) break;
         const uint32_t q = k * kPartThreads2 + threadIdx.x;
         if (q < p.g) cnt[q] = got[k];
       }
       __syncthreads();
+      const uint32_t capK = p.cap * K;
 #pragma unroll
       for (uint32_t q = 0; q < kPartPer; ++q) {
         if (sr[q] == 0xFFFFFFFFu) continue;
-        const uint32_t e = q * kPartThreads2 + threadIdx.x, sg = sr[q] >> 16;
-        const uint32_t pos = cnt[sg] + (sr[q] & 0xFFFFu);
+        const uint32_t e = q * kPartThreads2 + threadIdx.x, s = sr[q] >> 16;
+        const uint32_t pos = cnt[s] + (sr[q] & 0xFFFFu);
         uint32_t rc;
         uint64_t rb, ib;
         if (!retry_pass) {
           // optimistic layout: a pure function of the bucket plan
           rc = p.cap;
-          rb = p.r64 + static_cast<uint64_t>(sg) * p.cap * K;
-          ib = p.r32 + static_cast<uint64_t>(sg) * p.cap;
+          rb = p.r64 + static_cast<uint64_t>(s) * capK;
+          ib = p.r32 + static_cast<uint64_t>(s) * p.cap;
         } else {
-          rc = v.rcap[p.seg0 + sg];
-          rb = v.rbase[p.seg0 + sg];
-          ib = v.ibase[p.seg0 + sg];
+          rc = v.rcap[p.seg0 + s];
+          rb = v.rbase[p.seg0 + s];
+          ib = v.ibase[p.seg0 + s];
         }
         if (pos < rc) {
           v.area64[rb + pos] = key0s[q];
@@ -1494,7 +1548,7 @@ __device__ __forceinline__ void rank_buckets(const P& a, uint32_t m, const uint3
 // (P::kScratch items) and its kMsd2Buckets sub-counters.  The items of a
 // bucket are distinct: its minimum and maximum differ, the kMsd2Bits window
 // ending at their highest differing bit holds at least two digits, and every
-// sub-bucket shares one more bit than its parent, so the splitting ends.
+// sub-bucket is smaller than its parent, so the splitting ends.
 template <typename P>
 __device__ __forceinline__ void split_buckets(const P& a, uint32_t* area, uint32_t* aux,
                                               uint32_t* warp_tmp) {
@@ -1523,6 +1577,12 @@ __device__ __forceinline__ void split_buckets(const P& a, uint32_t* area, uint32
 #pragma unroll
     for (uint32_t k = 0; k < per; ++k) sub[threadIdx.x * per + k] = 0;
     block_min_max<P>(vmin, vmax, aux);
+    // distinct items always differ; equal ones (never produced by the
+    // encoding) would need no order, and skipping them keeps the loop finite
+    if (!P::lt(vmin, vmax)) {
+      __syncthreads();  // the copy and the minima are read before reuse
+      continue;
+    }
     const uint32_t hb = a.width(vmin, vmax);
     const uint32_t sh = hb > kMsd2Bits ? hb - kMsd2Bits : 0u;
     for (uint32_t i = threadIdx.x; i < m; i += kSegThreads)
@@ -1562,6 +1622,9 @@ template <int E, typename P, typename It>
 __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv, uint32_t bits, const P& a,
                                                   uint32_t* cnt, uint32_t* warp_tmp, uint32_t* aux) {
   const uint32_t sh = bits > kMsdBits ? bits - kMsdBits : 0u;
+  // items below 2^bits have digits below kMsdBuckets; the clamp keeps every
+  // counter access inside the counters whatever the items hold
+  const auto digit = [a, sh](const typename P::T& y) { return min(a.bits(y, sh), kMsdBuckets - 1); };
   constexpr uint32_t per = kMsdBuckets / kSegThreads;  // counters per thread
   static_assert(per == 16 && per * kSegThreads == kMsdBuckets, "16 counters per thread");
   // thread t's counters (buckets 16 t .. 16 t + 15) start at word 17 t: the
@@ -1573,7 +1636,7 @@ __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv,
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) atomicAdd(&cnt[slot(a.bits(P::of(x[j]), sh))], 1u);
+    if (j < nv) atomicAdd(&cnt[slot(digit(P::of(x[j])))], 1u);
   __syncthreads();
   // exclusive scan of the counts (thread t owns counters t*per .. t*per+per-1)
   uint32_t v[per], sum = 0, mx = 0;
@@ -1608,11 +1671,10 @@ __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv,
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) a.st(atomicAdd(&cnt[slot(a.bits(P::of(x[j]), sh))], 1u), P::of(x[j]));
+    if (j < nv) a.st(atomicAdd(&cnt[slot(digit(P::of(x[j])))], 1u), P::of(x[j]));
   __syncthreads();
   // cnt[slot(b)] is now the end of bucket b; bucket b spans [end(b-1), end(b))
-  rank_buckets<E>(a, cnt[slot(kMsdBuckets - 1)], cnt,
-                  [a, sh](const typename P::T& y) { return a.bits(y, sh); }, slot, 0u, list, n_list);
+  rank_buckets<E>(a, cnt[slot(kMsdBuckets - 1)], cnt, digit, slot, 0u, list, n_list);
   __syncthreads();
   if (tm > kMsdMaxBucket) split_buckets(a, cnt, aux, warp_tmp);  // block-uniform
   return true;

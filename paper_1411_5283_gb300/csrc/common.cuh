@@ -58,7 +58,10 @@ __host__ __device__ constexpr uint32_t auto_sample_max(uint32_t K) {
 constexpr uint32_t kAutoSampleEvery = 32;      // one stratified sample position per 32 words
 constexpr uint32_t kAutoMinWords = 65536;      // smaller inputs take the merge path
 constexpr uint64_t kAutoSlack = 1u << 18;      // extra elements of the third region
-constexpr uint32_t kAutoDirBytes = 528;        // first-byte directory per bucket (257 x u16)
+// splitter directory per bucket: (kAutoDir2Max + 1) u16 entries, enough for
+// two-byte codes of mixed-case letters (65 byte classes)
+constexpr uint32_t kAutoDir2Max = 65 * 65;
+constexpr uint32_t kAutoDirBytes = 8464;
 
 __host__ __device__ constexpr uint32_t auto_sample_cap(uint32_t K, uint64_t cap) {
   return static_cast<uint32_t>(
