@@ -1393,22 +1393,26 @@ __device__ __forceinline__ void scan_digit_counts(uint16_t* hist, uint32_t* warp
 // highest bit in which its items differ, its sub-buckets placed or listed the
 // same way, until the list is empty.  Returns false, with the items untouched
 // in registers, when a bucket holds more than the planes' scratch capacity:
-// then the radix passes run.  cnt holds 2^kMsdBits + 2^kMsdBits / 16 words;
-// aux holds kMsdAuxWords words.
+// then the radix passes run.  cnt holds kMsdBuckets counters, one padding
+// word after every kMsdBuckets / kSegThreads of them; aux holds kMsdAuxWords
+// words.
 constexpr uint32_t kMsdBits = 13;
 constexpr uint32_t kMsdBuckets = 1u << kMsdBits;
 constexpr uint32_t kMsdMaxBucket = 128;
 constexpr uint32_t kMsd2Bits = 10;
 constexpr uint32_t kMsd2Buckets = 1u << kMsd2Bits;
-// a split bucket is copied into the counter words the sub-counters leave free
-constexpr uint32_t kMsdScratchWords = kMsdBuckets - kMsd2Buckets;
+// the counter area: the index plane of a one-key segment, key plane 1 of a
+// two-key one; a split bucket is copied into the words the sub-counters leave
+// free
+constexpr uint32_t kMsdAreaWords = 8192;
+constexpr uint32_t kMsdScratchWords = kMsdAreaWords - kMsd2Buckets;
 // listed buckets are disjoint and larger than kMsdMaxBucket
 constexpr uint32_t kMsdList = auto_seg_cap(1) / (kMsdMaxBucket + 1) + 1;
 // warp minima and maxima (2 kRxWarps u64, then 2 kRxWarps u32), list, its size
 constexpr uint32_t kMsdAuxWords = 6 * kRxWarps + kMsdList + 1;
-// The counters, one padding word per 16, run kMsdBuckets / 16 words past the
-// counter area (into the next plane); the list lives this far into the radix
-// counter area, clear of them.
+// The padded counters run up to one word per thread past the counter area
+// (into the next plane); the list lives this far into the radix counter area,
+// clear of them.
 constexpr uint32_t kMsdAuxOffset = 1024;
 
 // Item planes of the bucket pass.  One-word items (Item64): the integer
@@ -1626,10 +1630,12 @@ __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv,
   // counter access inside the counters whatever the items hold
   const auto digit = [a, sh](const typename P::T& y) { return min(a.bits(y, sh), kMsdBuckets - 1); };
   constexpr uint32_t per = kMsdBuckets / kSegThreads;  // counters per thread
-  static_assert(per == 16 && per * kSegThreads == kMsdBuckets, "16 counters per thread");
-  // thread t's counters (buckets 16 t .. 16 t + 15) start at word 17 t: the
-  // threads of a warp touch 32 different banks when they walk their counters
-  const auto slot = [](uint32_t b) { return b + (b >> 4); };
+  static_assert(per * kSegThreads == kMsdBuckets && (per & (per - 1)) == 0 && per >= 2,
+                "a power-of-two number of counters per thread");
+  // thread t's counters (buckets per t .. per t + per - 1) start at word
+  // (per + 1) t: the threads of a warp touch 32 different banks when they walk
+  // their counters
+  const auto slot = [](uint32_t b) { return b + b / per; };
   uint32_t* mine = cnt + threadIdx.x * (per + 1);
 #pragma unroll
   for (uint32_t k = 0; k < per; ++k) mine[k] = 0;
@@ -2012,44 +2018,42 @@ constexpr uint32_t kHistThreads = 256;
 
 // Each thread counts in its own shared-memory column (no contention), then
 // the block adds its column sums to the global totals: one atomic per length
-// per block.
+// per block.  Lengths are read 16 per load, two loads in flight per thread.
+__device__ __forceinline__ void hist_count(uint32_t L, uint32_t W, uint32_t* col, bool& bad_zero,
+                                           bool& bad_long) {
+  bad_zero |= L == 0;
+  bad_long |= L > W;
+  if (L >= 1 && L <= W) atomicAdd(&col[L * kHistThreads], 1u);  // reduction: no read-back
+}
+
 __global__ void __launch_bounds__(kHistThreads)
 auto_hist_kernel(const uint8_t* __restrict__ len, uint32_t n_cap, const uint32_t* __restrict__ d_n,
                  uint32_t W, Ws ws, AutoView av) {
   __shared__ uint32_t cnt[kBins][kHistThreads];
   const AutoView& v = av;
   for (uint32_t L = 0; L < kBins; ++L) cnt[L][threadIdx.x] = 0;
+  uint32_t* col = &cnt[0][threadIdx.x];
   const uint32_t n = word_count(n_cap, d_n);
   bool bad_zero = false, bad_long = false;
-  const uint32_t stride = gridDim.x * kHistThreads;
-  if ((reinterpret_cast<uintptr_t>(len) & 3u) == 0) {
-    const uint32_t n4 = n / 4;
-    const uchar4* l4 = reinterpret_cast<const uchar4*>(len);
-    for (uint32_t q = blockIdx.x * kHistThreads + threadIdx.x; q < n4; q += stride) {
-      const uchar4 b = __ldg(l4 + q);
-      const uint32_t ls[4] = {b.x, b.y, b.z, b.w};
+  const uint32_t gtid = blockIdx.x * kHistThreads + threadIdx.x, stride = gridDim.x * kHistThreads;
+  // bytes before the first 16-byte boundary, then 16-byte groups, then the tail
+  const uint32_t head = min(n, static_cast<uint32_t>((16u - (reinterpret_cast<uintptr_t>(len) & 15u)) & 15u));
+  const uint32_t n16 = (n - head) / 16;
+  if (gtid < head) hist_count(len[gtid], W, col, bad_zero, bad_long);
+  const uint4* l16 = reinterpret_cast<const uint4*>(len + head);
+  for (uint32_t q = gtid; q < n16; q += 2 * stride) {
+    const uint4 a = __ldg(l16 + q);
+    const bool two = q + stride < n16;
+    const uint4 b = two ? __ldg(l16 + q + stride) : make_uint4(0, 0, 0, 0);
+    const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t L = ls[k];
-        bad_zero |= L == 0;
-        bad_long |= L > W;
-        if (L >= 1 && L <= W) atomicAdd(&cnt[L][threadIdx.x], 1u);  // reduction: no read-back
-      }
-    }
-    for (uint32_t i = 4 * n4 + blockIdx.x * kHistThreads + threadIdx.x; i < n; i += stride) {
-      const uint32_t L = len[i];
-      bad_zero |= L == 0;
-      bad_long |= L > W;
-      if (L >= 1 && L <= W) atomicAdd(&cnt[L][threadIdx.x], 1u);
-    }
-  } else {
-    for (uint32_t i = blockIdx.x * kHistThreads + threadIdx.x; i < n; i += stride) {
-      const uint32_t L = len[i];
-      bad_zero |= L == 0;
-      bad_long |= L > W;
-      if (L >= 1 && L <= W) atomicAdd(&cnt[L][threadIdx.x], 1u);
+    for (int k = 0; k < 16; ++k) hist_count((wa[k >> 2] >> (8 * (k & 3))) & 255u, W, col, bad_zero, bad_long);
+    if (two) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) hist_count((wb[k >> 2] >> (8 * (k & 3))) & 255u, W, col, bad_zero, bad_long);
     }
   }
+  for (uint32_t i = head + 16 * n16 + gtid; i < n; i += stride) hist_count(len[i], W, col, bad_zero, bad_long);
   __syncthreads();
   // warp w sums lengths w, w + 8, ...: lanes add 8 columns each, then reduce
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
@@ -2110,12 +2114,13 @@ static_assert((kMsdAuxOffset + kMsdAuxWords) * 4 <= kRxWarps * kRxDigits * sizeo
 static_assert(auto_seg_cap(1) / 2 * 12 <= auto_seg_cap(1) * 8 && auto_seg_cap(2) * 4 <= auto_seg_cap(2) / 2 * 8 &&
                   auto_seg_cap(2) / 2 * 8 + auto_seg_cap(2) * 4 >= kMsdBuckets * 4,
               "two-part item planes and counters fit the segment planes");
-// one-key segments: counters in the index plane and the first kMsdBuckets / 16
-// words of the radix counters; two-key segments: in key plane 1 and the first
-// words of the index plane
-static_assert(kMsdBuckets / 16 <= kMsdAuxOffset && kMsdBuckets / 16 <= auto_seg_cap(2),
+// one-key segments: counters in the index plane and the first words of the
+// radix counters; two-key segments: in key plane 1 and the first words of the
+// index plane
+static_assert(kMsdBuckets + kSegThreads <= kMsdAreaWords + kMsdAuxOffset && kMsdBuckets <= kMsdAreaWords &&
+                  kMsdBuckets + kSegThreads <= kMsdAreaWords + auto_seg_cap(2),
               "padded bucket counters stay clear of the split list");
-static_assert(2 * P64::kScratch + kMsd2Buckets <= kMsdBuckets && 3 * P96::kScratch + kMsd2Buckets <= kMsdBuckets &&
+static_assert(2 * P64::kScratch + kMsd2Buckets <= kMsdAreaWords && 3 * P96::kScratch + kMsd2Buckets <= kMsdAreaWords &&
                   auto_seg_cap(1) < 65536,
               "split copy and sub-counters fit the counter area; list entries pack start and size");
 // two CTAs per SM: dynamic + static (at most 256 bytes: the workspace view and
