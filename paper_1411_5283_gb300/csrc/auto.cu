@@ -51,6 +51,18 @@ constexpr uint32_t kCursorStride = 32;
 // ---------------------------------------------------------------------------
 // Device view of the AUTO area
 // ---------------------------------------------------------------------------
+// Per-bucket plan, a pure function of the bucket counts.
+struct BucketPlan {
+  uint32_t g;        // segments
+  uint32_t cap;      // region capacity of each segment
+  uint32_t seg0;     // first global segment id
+  uint32_t K;        // key words
+  uint64_t r64, r32; // first u64 / u32 of the bucket's regions
+  uint32_t s64, s32; // first u64 / u32 of the bucket's sample planes
+  uint32_t scap;     // sample capacity of the bucket
+  uint32_t spl_off;  // byte offset of the bucket's splitters in the table
+};
+
 struct AutoHdr {
   uint32_t overflow;        // a partition slot fell past its region
   uint32_t retry;           // the retry pass is armed
@@ -62,6 +74,7 @@ struct AutoHdr {
   uint32_t next_seg;        // segments handed out to the sorting CTAs
   uint32_t band, bor;       // AND and OR of every byte inside a word: bounds of their range
   uint32_t imax;            // largest word index
+  BucketPlan plans[kBins];  // per length bucket, from the offsets
 };
 static_assert(sizeof(AutoHdr) <= 4096, "the header fits its page of the AUTO area");
 
@@ -133,17 +146,6 @@ __host__ __device__ AutoView auto_view(const Ws& ws, uint32_t W) {
   return v;
 }
 
-// Per-bucket plan, a pure function of the bucket counts.
-struct BucketPlan {
-  uint32_t g;        // segments
-  uint32_t cap;      // region capacity of each segment
-  uint32_t seg0;     // first global segment id
-  uint32_t K;        // key words
-  uint64_t r64, r32; // first u64 / u32 of the bucket's regions
-  uint32_t s64, s32; // first u64 / u32 of the bucket's sample planes
-  uint32_t scap;     // sample capacity of the bucket
-  uint32_t spl_off;  // byte offset of the bucket's splitters in the table
-};
 
 __host__ __device__ __forceinline__ uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
 
@@ -233,10 +235,10 @@ __device__ __forceinline__ uint32_t word_count(uint32_t n_cap, const uint32_t* d
 }
 
 __device__ void load_plans(BucketPlan* plans, uint32_t* s_off, const uint32_t* d_off, uint32_t W,
-                           uint64_t cap) {
+                           const AutoHdr* hdr) {
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x >= 1 && threadIdx.x <= W) plans[threadIdx.x] = plan_for(s_off, threadIdx.x, cap);
+  if (threadIdx.x >= 1 && threadIdx.x <= W) plans[threadIdx.x] = hdr->plans[threadIdx.x];
   __syncthreads();
 }
 
@@ -251,7 +253,7 @@ auto_sample_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
   __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ uint32_t thr[kMaxW + 1], bcnt[kMaxW + 1], bbase[kMaxW + 1];
   const AutoView& v = av;
-  load_plans(plans, s_off, d_off, W, v.cap);
+  load_plans(plans, s_off, d_off, W, v.hdr);
   // Acceptance probability per bucket: about 20 samples per expected segment
   // (segments expect 2730 / 1365 / 682 words for 1 / 2 / >= 3 keys, positions
   // are one per 32 words), but never more than 90 % of the bucket's sample
@@ -498,7 +500,7 @@ auto_spl_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, Auto
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
   if (threadIdx.x == 0) {
-    p = plan_for(s_off, L, v.cap);
+    p = v.hdr->plans[L];
     if (L == W && j == 0) {
       const BucketPlan last = p;
       v.hdr->G = last.seg0 + last.g;
@@ -622,7 +624,7 @@ auto_spl_select_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, Au
   const uint32_t L = blockIdx.x + 1, j = blockIdx.y;
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
+  if (threadIdx.x == 0) p = v.hdr->plans[L];
   __syncthreads();
   if (p.g < 2) return;
   const uint32_t m = min(v.hdr->samp_cnt[L], p.scap);
@@ -720,7 +722,7 @@ auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoV
   const uint32_t L = blockIdx.x + 1;
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) p = plan_for(s_off, L, v.cap);
+  if (threadIdx.x == 0) p = v.hdr->plans[L];
   __syncthreads();
   if (p.K <= 2) segment_codes(v, p, L);
   if (p.g < 2) return;
@@ -934,7 +936,7 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
   if (threadIdx.x <= W) {
-    const BucketPlan bp = threadIdx.x ? plan_for(s_off, threadIdx.x, v.cap) : BucketPlan{};
+    const BucketPlan bp = v.hdr->plans[threadIdx.x];
     plans[threadIdx.x] = PartPlan{bp.g, bp.seg0, bp.spl_off, bp.cap, bp.r64, bp.r32};
   }
   stage_key_bases(s_off, W, kb);
@@ -1095,36 +1097,55 @@ auto_layout_kernel(uint32_t W, Ws ws, AutoView av) {
   const AutoView& v = av;
   const uint32_t G = v.hdr->G;
   const bool redo = v.hdr->overflow != 0;
+  // thread t owns segments [t per, t per + per); their counts and key word
+  // counts are read in batches of kLayoutBatch, every load of a batch in
+  // flight together, and kept for the second pass when one batch covers them
+  constexpr uint32_t kLayoutBatch = 8;
   const uint32_t per = (G + blockDim.x - 1) / blockDim.x;
   const uint32_t b = threadIdx.x * per, e = min(G, b + per);
+  uint32_t xs[kLayoutBatch], ks[kLayoutBatch];
+  const auto load = [&](uint32_t j0) {
+#pragma unroll
+    for (uint32_t u = 0; u < kLayoutBatch; ++u) {
+      const uint32_t j = j0 + u;
+      xs[u] = j < e ? v.cursor[j * kCursorStride] : 0u;
+      ks[u] = j < e ? keys_for_len(v.segL[j]) : 1u;
+    }
+  };
   // exclusive scans of counts (output ranks) and, for a retry, of exact
   // regions (index area) and region x K (key area)
   uint32_t c = 0, c4 = 0, ck = 0;
-  for (uint32_t j = b; j < e; ++j) {
-    const uint32_t x = v.cursor[j * kCursorStride];
-    const uint32_t K = keys_for_len(v.segL[j]);
-    c += x;
-    c4 += exact_region(x, K);
-    ck += exact_region(x, K) * K;
+  for (uint32_t j0 = b; j0 < e; j0 += kLayoutBatch) {
+    load(j0);
+#pragma unroll
+    for (uint32_t u = 0; u < kLayoutBatch; ++u) {
+      c += xs[u];
+      c4 += exact_region(xs[u], ks[u]);
+      ck += exact_region(xs[u], ks[u]) * ks[u];
+    }
   }
   uint32_t tot, tot4, totk;
   uint32_t run = block_exclusive_scan(c, tmp, &tot);
   uint32_t run4 = block_exclusive_scan(c4, tmp, &tot4);
   uint32_t runk = block_exclusive_scan(ck, tmp, &totk);
   const bool fits = tot4 <= v.size32 && totk <= v.size64;
-  for (uint32_t j = b; j < e; ++j) {
-    const uint32_t x = v.cursor[j * kCursorStride];
-    const uint32_t K = keys_for_len(v.segL[j]);
-    v.outbase[j] = run;
-    run += x;
-    if (redo && fits) {
-      const uint32_t r = exact_region(x, K);
-      v.rcap[j] = r;
-      v.ibase[j] = run4;
-      v.rbase[j] = runk;
-      run4 += r;
-      runk += r * K;
-      v.cursor[j * kCursorStride] = 0;
+  for (uint32_t j0 = b; j0 < e; j0 += kLayoutBatch) {
+    if (per > kLayoutBatch) load(j0);  // block-uniform
+#pragma unroll
+    for (uint32_t u = 0; u < kLayoutBatch; ++u) {
+      const uint32_t j = j0 + u;
+      if (j >= e) break;
+      v.outbase[j] = run;
+      run += xs[u];
+      if (redo && fits) {
+        const uint32_t r = exact_region(xs[u], ks[u]);
+        v.rcap[j] = r;
+        v.ibase[j] = run4;
+        v.rbase[j] = runk;
+        run4 += r;
+        runk += r * ks[u];
+        v.cursor[j * kCursorStride] = 0;
+      }
     }
   }
   if (threadIdx.x == 0 && redo) {
@@ -2071,7 +2092,7 @@ auto_hist_kernel(const uint8_t* __restrict__ len, uint32_t n_cap, const uint32_t
 // Bucket offsets off[L] (words shorter than L) from the totals; also resets
 // the per-call state of the sample sort.
 __global__ void auto_offsets_kernel(uint32_t W, Ws ws, AutoView av, uint32_t* __restrict__ off) {
-  __shared__ uint32_t tot[kBins];
+  __shared__ uint32_t tot[kBins], so[kMaxW + 2];
   const AutoView& v = av;
   const uint32_t L = threadIdx.x;
   if (L < kBins) tot[L] = (L >= 1 && L <= W) ? v.hdr->total[L] : 0u;
@@ -2080,7 +2101,11 @@ __global__ void auto_offsets_kernel(uint32_t W, Ws ws, AutoView av, uint32_t* __
     uint32_t s = 0;
     for (uint32_t l = 1; l < L && l <= W; ++l) s += tot[l];
     off[L] = s;
+    so[L] = s;
   }
+  __syncthreads();
+  // every later kernel reads its buckets' plans from here
+  if (L < kBins) v.hdr->plans[L] = (L >= 1 && L <= W) ? plan_for(so, L, v.cap) : BucketPlan{};
   if (L < kMaxW + 2) ws.hdr->final_buf[L] = 0;
   if (L < kBins) {
     v.hdr->samp_cnt[L] = 0;
