@@ -1665,13 +1665,14 @@ __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv,
   for (int j = 0; j < E; ++j)
     if (j < nv) atomicAdd(&cnt[slot(digit(P::of(x[j])))], 1u);
   __syncthreads();
-  // exclusive scan of the counts (thread t owns counters t*per .. t*per+per-1)
-  uint32_t v[per], sum = 0, mx = 0;
+  // exclusive scan of the counts (thread t owns counters t*per .. t*per+per-1;
+  // read twice rather than held, which keeps registers for the items)
+  uint32_t sum = 0, mx = 0;
 #pragma unroll
   for (uint32_t k = 0; k < per; ++k) {
-    v[k] = mine[k];
-    sum += v[k];
-    mx = v[k] > mx ? v[k] : mx;
+    const uint32_t c = mine[k];
+    sum += c;
+    mx = c > mx ? c : mx;
   }
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t inc = warp_inclusive_scan(sum);
@@ -1689,8 +1690,9 @@ __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv,
   uint32_t run = __shfl_sync(0xffffffffu, tupto - tw, warp) + inc - sum;
 #pragma unroll
   for (uint32_t k = 0; k < per; ++k) {
+    const uint32_t c = mine[k];
     mine[k] = run;  // bucket start, then its cursor
-    run += v[k];
+    run += c;
   }
   uint32_t* list = aux + 6 * kRxWarps;
   uint32_t* n_list = list + kMsdList;
@@ -1781,24 +1783,49 @@ __device__ __forceinline__ bool radix_sort_items(Get get, uint32_t c, uint32_t b
 }
 
 // Sorts the segment's items (converted from the key and index planes, which
-// are then reused as the item store) and writes the output records.  The
-// buffer comes as an offset into dynamic shared memory, so that every access
-// compiles to a shared-memory instruction.  Not inlined: the caller's segment
-// loop keeps its own state live, and the items need the registers.
+// are then reused as the item store); k1_write then writes the output
+// records.  The buffer comes as an offset into dynamic shared memory, so that
+// every access compiles to a shared-memory instruction.  Not inlined, and
+// apart from the writing: the items need the registers, and the writing loop
+// keeps its parameters in registers of its own.  Returns the shared-memory
+// offset of the plane that holds the sorted indices of two-part items (0 for
+// one-word items, whose indices are their low bits).
 template <typename It, int E>
-__device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, ByteCode bc, uint32_t kb,
-                                      uint32_t ib, uint32_t W, uint32_t ob, uint8_t* out_rec,
-                                      uint32_t* out_perm) {
+__device__ __noinline__ uint32_t k1_radix(uint32_t buf_off, uint32_t c, ByteCode bc, uint32_t kb,
+                                          uint32_t ib) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   constexpr uint32_t C = auto_seg_cap(1);
   uint64_t* kp = reinterpret_cast<uint64_t*>(smem_raw + buf_off);
   uint32_t* ip = reinterpret_cast<uint32_t*>(kp + C);
   uint16_t* hist = reinterpret_cast<uint16_t*>(ip + C);
   uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
+  uint32_t idx_off = 0;
   if constexpr (sizeof(It) == sizeof(Item64)) {
     auto get = [=](uint32_t p) { return Item64{(bc.encode(kp[p]) << ib) | ip[p]}; };
     // the index plane is free once the items are in registers: bucket counters
     radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp, ip, P64{kp});
+  } else {
+    auto get = [=](uint32_t p) { return Item96{bc.encode(kp[p]), ip[p]}; };
+    // up to half the capacity, the bucket pass keeps the codes in the key
+    // plane and the indices in its upper half, the counters in the index plane
+    constexpr uint32_t H = C / 2;
+    const P96 bp{kp, reinterpret_cast<uint32_t*>(kp + H), ib};
+    const bool bucketed = radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp,
+                                                           c <= H ? ip : nullptr, bp);
+    idx_off = buf_off + (bucketed ? H * 8 : C * 8);
+  }
+  __syncthreads();
+  return idx_off;
+}
+
+// Output records and permutation of a sorted one-key segment: codes (with the
+// index in their low ib bits when idx_off is 0, else in the plane at idx_off)
+// in the key plane at buf_off.
+__device__ __noinline__ void k1_write(uint32_t buf_off, uint32_t idx_off, uint32_t c, ByteCode bc, uint32_t ib,
+                                      uint32_t W, uint32_t ob, uint8_t* out_rec, uint32_t* out_perm) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint64_t* kp = reinterpret_cast<const uint64_t*>(smem_raw + buf_off);
+  if (idx_off == 0) {
     const uint64_t imask = (1ull << ib) - 1;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       const uint64_t v = kp[r];
@@ -1808,14 +1835,7 @@ __device__ __noinline__ void k1_radix(uint32_t buf_off, uint32_t c, ByteCode bc,
       write_word<1>(W, out_rec, out_perm, ob + r, e);
     }
   } else {
-    auto get = [=](uint32_t p) { return Item96{bc.encode(kp[p]), ip[p]}; };
-    // up to half the capacity, the bucket pass keeps the codes in the key
-    // plane and the indices in its upper half, the counters in the index plane
-    constexpr uint32_t H = C / 2;
-    const P96 bp{kp, reinterpret_cast<uint32_t*>(kp + H), ib};
-    const bool bucketed = radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{kp, ip}, hist, warp_tmp,
-                                                           c <= H ? ip : nullptr, bp);
-    const uint32_t* op = bucketed ? bp.i : ip;
+    const uint32_t* op = reinterpret_cast<const uint32_t*>(smem_raw + idx_off);
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       Elem<1> e;
       e.k[0] = bc.decode(kp[r]);
@@ -1871,9 +1891,8 @@ __device__ __forceinline__ void decode16(const uint32_t* f, uint64_t code, Elem<
 }
 
 template <typename It, int E>
-__device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32_t* f, uint32_t kb,
-                                      uint32_t ib, uint32_t W, uint32_t ob, uint8_t* out_rec,
-                                      uint32_t* out_perm) {
+__device__ __noinline__ uint32_t k2_radix(uint32_t buf_off, uint32_t c, const uint32_t* f, uint32_t kb,
+                                          uint32_t ib) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   constexpr uint32_t C = auto_seg_cap(2);
   static_assert(2 * C >= kMsdBuckets, "plane 1 holds the bucket counters");
@@ -1882,10 +1901,31 @@ __device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32
   uint32_t* ip = reinterpret_cast<uint32_t*>(k1p + C);
   uint16_t* hist = reinterpret_cast<uint16_t*>(ip + C);
   uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
+  uint32_t idx_off = 0;
   if constexpr (sizeof(It) == sizeof(Item64)) {
     auto get = [=](uint32_t p) { return Item64{(encode16(f, k0p[p], k1p[p]) << ib) | ip[p]}; };
     radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{k0p}, hist, warp_tmp,
                                      reinterpret_cast<uint32_t*>(k1p), P64{k0p});
+  } else {
+    auto get = [=](uint32_t p) { return Item96{encode16(f, k0p[p], k1p[p]), ip[p]}; };
+    // the bucket pass keeps the codes in plane 0 and the indices in the lower
+    // half of plane 1; its counters take the upper half and the index plane
+    const P96 bp{k0p, reinterpret_cast<uint32_t*>(k1p), ib};
+    const bool bucketed = radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{k0p, ip}, hist, warp_tmp,
+                                                           reinterpret_cast<uint32_t*>(k1p + C / 2), bp);
+    idx_off = buf_off + (bucketed ? C * 8 : 2 * C * 8);
+  }
+  __syncthreads();
+  return idx_off;
+}
+
+// Output records and permutation of a sorted two-key segment (as k1_write).
+__device__ __noinline__ void k2_write(uint32_t buf_off, uint32_t idx_off, uint32_t c, const uint32_t* f,
+                                      uint32_t ib, uint32_t W, uint32_t ob, uint8_t* out_rec,
+                                      uint32_t* out_perm) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint64_t* k0p = reinterpret_cast<const uint64_t*>(smem_raw + buf_off);
+  if (idx_off == 0) {
     const uint64_t imask = (1ull << ib) - 1;
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       const uint64_t v = k0p[r];
@@ -1895,13 +1935,7 @@ __device__ __noinline__ void k2_radix(uint32_t buf_off, uint32_t c, const uint32
       write_word<2>(W, out_rec, out_perm, ob + r, e);
     }
   } else {
-    auto get = [=](uint32_t p) { return Item96{encode16(f, k0p[p], k1p[p]), ip[p]}; };
-    // the bucket pass keeps the codes in plane 0 and the indices in the lower
-    // half of plane 1; its counters take the upper half and the index plane
-    const P96 bp{k0p, reinterpret_cast<uint32_t*>(k1p), ib};
-    const bool bucketed = radix_sort_items<It, Store96, E>(get, c, kb + ib, ib, Store96{k0p, ip}, hist, warp_tmp,
-                                                           reinterpret_cast<uint32_t*>(k1p + C / 2), bp);
-    const uint32_t* op = bucketed ? bp.i : ip;
+    const uint32_t* op = reinterpret_cast<const uint32_t*>(smem_raw + idx_off);
     for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) {
       Elem<2> e;
       decode16(f, k0p[r], e);
@@ -1928,13 +1962,15 @@ __device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const A
   if (kb > 64) return false;  // block-uniform
   const uint32_t ob = v.outbase[seg];
   const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);
+  uint32_t idx_off;
   if (kb + ib <= 64) {
-    if (c <= 4 * kSegThreads) k2_radix<Item64, 4>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
-    else k2_radix<Item64, 8>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
+    if (c <= 4 * kSegThreads) idx_off = k2_radix<Item64, 4>(off, c, s_f2, kb, ib);
+    else idx_off = k2_radix<Item64, 8>(off, c, s_f2, kb, ib);
   } else {
-    if (c <= 4 * kSegThreads) k2_radix<Item96, 4>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
-    else k2_radix<Item96, 8>(off, c, s_f2, kb, ib, W, ob, out_rec, out_perm);
+    if (c <= 4 * kSegThreads) idx_off = k2_radix<Item96, 4>(off, c, s_f2, kb, ib);
+    else idx_off = k2_radix<Item96, 8>(off, c, s_f2, kb, ib);
   }
+  k2_write(off, idx_off, c, s_f2, ib, W, ob, out_rec, out_perm);
   return true;
 }
 
@@ -1954,15 +1990,17 @@ __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const A
   const uint32_t kb = __ldg(sf + 16), ib = __ldg(sf + 17);
   const uint32_t ob = v.outbase[seg];
   const uint32_t off = static_cast<uint32_t>(buf + 16 - smem_base);
+  uint32_t idx_off;
   if (kb + ib <= 64) {
-    if (c <= 4 * kSegThreads) k1_radix<Item64, 4>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
-    else if (c <= 8 * kSegThreads) k1_radix<Item64, 8>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
-    else k1_radix<Item64, 16>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
+    if (c <= 4 * kSegThreads) idx_off = k1_radix<Item64, 4>(off, c, bc, kb, ib);
+    else if (c <= 8 * kSegThreads) idx_off = k1_radix<Item64, 8>(off, c, bc, kb, ib);
+    else idx_off = k1_radix<Item64, 16>(off, c, bc, kb, ib);
   } else {
-    if (c <= 4 * kSegThreads) k1_radix<Item96, 4>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
-    else if (c <= 8 * kSegThreads) k1_radix<Item96, 8>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
-    else k1_radix<Item96, 16>(off, c, bc, kb, ib, W, ob, out_rec, out_perm);
+    if (c <= 4 * kSegThreads) idx_off = k1_radix<Item96, 4>(off, c, bc, kb, ib);
+    else if (c <= 8 * kSegThreads) idx_off = k1_radix<Item96, 8>(off, c, bc, kb, ib);
+    else idx_off = k1_radix<Item96, 16>(off, c, bc, kb, ib);
   }
+  k1_write(off, idx_off, c, bc, ib, W, ob, out_rec, out_perm);
 }
 
 // Persistent CTAs (two per SM) walk the segments: bulk-copy the segment into
