@@ -33,6 +33,8 @@
 //                          the segment's output base; a segment larger than
 //                          shared memory (only after a retry) is sorted in
 //                          chunks and merged in global memory
+#include <type_traits>
+
 #include "block_scan.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -1349,12 +1351,14 @@ struct Item96 {
 };
 struct Store64 {
   uint64_t* a;
+  __device__ uint64_t* k_or_a() const { return a; }
   __device__ Item64 load(uint32_t p) const { return Item64{a[p]}; }
   __device__ void store(uint32_t p, const Item64& x) const { a[p] = x.v; }
 };
 struct Store96 {
   uint64_t* k;
   uint32_t* i;
+  __device__ uint64_t* k_or_a() const { return k; }
   __device__ Item96 load(uint32_t p) const { return Item96{k[p], i[p]}; }
   __device__ void store(uint32_t p, const Item96& x) const {
     k[p] = x.k;
@@ -1709,18 +1713,30 @@ __device__ __forceinline__ bool bucket_sort_items(const It (&x)[E], uint32_t nv,
   return true;
 }
 
-// Stable LSD radix sort of c items, held in registers: warp w owns positions
+// Stable LSD radix sort of c items in the store st: warp w owns positions
 // [w S, w S + S) (S = ceil(c / warps) rounded up to 32), lane l holds
-// position w S + 32 j + l in x[j], read through get(p).  Each pass ranks the
-// items of a warp in position order (running per-warp digit counters
-// hist[w][*] plus the lanes below with the same digit), scans the counters,
-// and scatters every item to its new position in the store.  The sorted items
-// end in st[0, c).  With bucket counters given, the bucket pass is tried
-// first; when it succeeds (the return value) the items end in bp[0, c).
-template <typename It, typename St, int E, typename Get, typename BP>
-__device__ __forceinline__ bool radix_sort_items(Get get, uint32_t c, uint32_t bits, uint32_t ib,
-                                                 St st, uint16_t* hist, uint32_t* warp_tmp,
-                                                 uint32_t* bucket_cnt, const BP& bp) {
+// position w S + 32 j + l in x[j].  Each pass ranks the items of a warp in
+// position order (running per-warp digit counters hist[w][*] plus the lanes
+// below with the same digit), scans the counters, and scatters every item to
+// its new position in the store.  The sorted items end in st[0, c).  The
+// planes and counters come as shared-memory offsets (a_off: the one-word
+// items or the codes, i_off: the indices of two-part items); not inlined, so
+// that the bucket pass, which nearly always succeeds, keeps registers of its
+// own.
+template <typename It, int E>
+__device__ __noinline__ void radix_passes(uint32_t a_off, uint32_t i_off, uint32_t hist_off, uint32_t c,
+                                          uint32_t bits, uint32_t ib) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  using St = typename std::conditional<sizeof(It) == sizeof(Item64), Store64, Store96>::type;
+  St st;
+  if constexpr (sizeof(It) == sizeof(Item64)) {
+    st = Store64{reinterpret_cast<uint64_t*>(smem_raw + a_off)};
+    (void)i_off;
+  } else {
+    st = Store96{reinterpret_cast<uint64_t*>(smem_raw + a_off), reinterpret_cast<uint32_t*>(smem_raw + i_off)};
+  }
+  uint16_t* hist = reinterpret_cast<uint16_t*>(smem_raw + hist_off);
+  uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t S = ((c + kRxWarps - 1) / kRxWarps + 31) & ~31u;
   const uint32_t w0 = warp * S, p0 = w0 + lane, lt = lanemask_lt();
@@ -1731,14 +1747,8 @@ __device__ __forceinline__ bool radix_sort_items(Get get, uint32_t c, uint32_t b
   It x[E];
 #pragma unroll
   for (int j = 0; j < E; ++j)
-    if (j < nv) x[j] = get(p0 + 32 * j);
-  // every item is read before the first pass scatters into the store
+    if (j < nv) x[j] = st.load(p0 + 32 * j);
   __syncthreads();
-  // byte-recoded keys spread their top bits: the bucket pass is tried first
-  if (bucket_cnt && bits > 8 &&
-      bucket_sort_items<E>(x, nv, bits, bp, bucket_cnt, warp_tmp,
-                           reinterpret_cast<uint32_t*>(hist) + kMsdAuxOffset))
-    return true;
   uint32_t rk[(E + 1) / 2];  // ranks, two 16-bit fields per word
   for (uint32_t s = 0; s < bits; s += 8) {
     for (uint32_t i = lane; i < kRxDigits; i += 32) row[i] = 0;
@@ -1779,6 +1789,43 @@ __device__ __forceinline__ bool radix_sort_items(Get get, uint32_t c, uint32_t b
         if (j < nv) x[j] = st.load(p0 + 32 * j);
     }
   }
+}
+
+// Sorts c items read through get(p): the bucket pass (bucket counters given)
+// into bp, else the radix passes into st; returns whether the bucket pass
+// did it.  Items are held in registers as in radix_passes.
+template <typename It, typename St, int E, typename Get, typename BP>
+__device__ __forceinline__ bool radix_sort_items(Get get, uint32_t c, uint32_t bits, uint32_t ib,
+                                                 St st, uint16_t* hist, uint32_t* warp_tmp,
+                                                 uint32_t* bucket_cnt, const BP& bp) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t S = ((c + kRxWarps - 1) / kRxWarps + 31) & ~31u;
+  const uint32_t p0 = warp * S + lane;
+  const uint32_t nr = S / 32, nv = min(nr, c > p0 ? (c - p0 + 31) / 32 : 0u);
+  It x[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (j < nv) x[j] = get(p0 + 32 * j);
+  // every item is read before the first pass scatters into the store
+  __syncthreads();
+  // byte-recoded keys spread their top bits: the bucket pass is tried first
+  if (bucket_cnt && bits > 8 &&
+      bucket_sort_items<E>(x, nv, bits, bp, bucket_cnt, warp_tmp,
+                           reinterpret_cast<uint32_t*>(hist) + kMsdAuxOffset))
+    return true;
+  // the items go to the store at their positions, the radix passes take them
+  // from there
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (j < nv) st.store(p0 + 32 * j, x[j]);
+  __syncthreads();
+  const auto off = [](const void* q) {
+    return static_cast<uint32_t>(reinterpret_cast<const uint8_t*>(q) - smem_raw);
+  };
+  uint32_t i_off = 0;
+  if constexpr (sizeof(It) != sizeof(Item64)) i_off = off(st.i);
+  radix_passes<It, E>(off(st.k_or_a()), i_off, off(hist), c, bits, ib);
   return false;
 }
 
