@@ -803,13 +803,14 @@ auto_bucket_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
     __syncthreads();
     uint32_t L[kBucketPer], r[kBucketPer];
     uint64_t k0[kBucketPer];
-    // lengths and first key words first: the record reads overlap the counting
+    // lengths and first key words first, all loads in flight together (the
+    // record read does not wait for the length): they overlap the counting
 #pragma unroll
     for (uint32_t q = 0; q < kBucketPer; ++q) {
       const uint32_t i = t0 + q * kBucketThreads + threadIdx.x;
       const uint32_t l = i < n ? len[i] : 0u;
       L[q] = (l >= 1 && l <= W) ? l : 0u;  // bad lengths are flagged by the histogram
-      k0[q] = L[q] ? __ldg(reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W)) : 0ull;
+      k0[q] = i < n ? __ldg(reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W)) : 0ull;
     }
 #pragma unroll
     for (uint32_t q = 0; q < kBucketPer; ++q) r[q] = L[q] ? atomicAdd(&cnt[L[q]], 1u) : 0u;
@@ -2040,6 +2041,7 @@ __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const A
   uint32_t idx_off;
   if (kb + ib <= 64) {
     if (c <= 4 * kSegThreads) idx_off = k1_radix<Item64, 4>(off, c, bc, kb, ib);
+    else if (c <= 6 * kSegThreads) idx_off = k1_radix<Item64, 6>(off, c, bc, kb, ib);
     else if (c <= 8 * kSegThreads) idx_off = k1_radix<Item64, 8>(off, c, bc, kb, ib);
     else idx_off = k1_radix<Item64, 16>(off, c, bc, kb, ib);
   } else {
