@@ -859,12 +859,13 @@ auto_bucket_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
 // the elements.  The bucket's splitter table is staged in shared memory when
 // it fits.  A slot past the region's end only counts and raises the overflow
 // flag (the retry pass then runs on exact regions).
-constexpr uint32_t kPartThreads2 = 512;
+constexpr uint32_t kPartThreads2 = 1024;  // one CTA per SM: tiles of 4,096 elements
 constexpr uint32_t kPartPer = 4;
 constexpr uint32_t kPartTile = kPartThreads2 * kPartPer;
 constexpr uint32_t kPartCounters = 8192;                  // segments per bucket counted in shared memory
-constexpr uint32_t kPartSplSmem = 72 * 1024;              // bucket splitter table staged up to this size
+constexpr uint32_t kPartSplSmem = 160 * 1024;             // bucket splitter table staged up to this size
 constexpr size_t kPartSmem = kPartCounters * 4 + kPartSplSmem;
+static_assert(kPartSmem + 4096 <= 227 * 1024, "the partition CTA's shared memory fits an SM");
 
 // Segments (indices within the bucket) of a thread's kPartPer elements (first
 // key words k0, input indices i; active[u] false for none), in a bucket whose
@@ -926,7 +927,7 @@ __device__ __forceinline__ void find_segments(const uint8_t* tab, const DirShape
   for (uint32_t u = 0; u < kPartPer; ++u) seg[u] = lo[u];
 }
 
-__global__ void __launch_bounds__(kPartThreads2, 2)
+__global__ void __launch_bounds__(kPartThreads2, 1)
 auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_pass, Ws ws,
                       AutoView av) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -2246,7 +2247,7 @@ cudaError_t partition(uint32_t W, const uint32_t* d_off, const Ws& ws, const Aut
   static size_t set = 0;
   cudaError_t e = ensure_smem(auto_partition_kernel, kPartSmem, &set);
   if (e != cudaSuccess) return e;
-  const uint32_t grid = static_cast<uint32_t>(g_sm_count) * 2;
+  const uint32_t grid = static_cast<uint32_t>(g_sm_count);
   BSORT_LAUNCH(retry ? "auto_partition_retry" : "auto_partition", auto_partition_kernel, grid,
                kPartThreads2, kPartSmem, s, W, d_off, retry, ws, v);
   return cudaGetLastError();
