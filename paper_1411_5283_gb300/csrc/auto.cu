@@ -3,36 +3,47 @@
 // Same answer as the paper's phases 2-3 and the concatenation (§3
 // Methodology, "Pre-processing"): every word ordered by (length, bytes, input
 // index).  Phase 2's length buckets are refined into key-range segments small
-// enough for one CTA's shared memory, so the words cross HBM about twice
-// instead of once per merge pass:
+// enough for one CTA's shared memory, so each word crosses HBM a fixed number
+// of times instead of once per merge pass:
 //
+//   auto_hist_kernel       words per length (phase 2's counts)
+//   auto_offsets_kernel    bucket offsets and every bucket's segment plan
 //   auto_sample_kernel     stratified sample (one position per 32 words, kept
 //                          with probability 1/4, 1/2, 1 for 1, 2, >= 3 key
 //                          words: about 20 samples per expected segment),
-//                          grouped by length bucket (phase 2's sub-arrays)
-//   auto_spl_sort_kernel   eight CTAs per bucket sort chunks of its samples;
-//                          every segment gets a region of the shared-memory
-//                          capacity, three times its expected count
+//                          grouped by length bucket
+//   auto_bucket_kernel     phase 2's sub-arrays: every word's key words and
+//                          index go to its length's staging planes; the AND
+//                          and OR of all bytes inside words bound their range
+//   auto_spl_sort_kernel   eight CTAs per bucket sort chunks of its samples
 //   auto_spl_select_kernel each sample's rank across the sorted chunks (binary
 //                          search) picks the g_L - 1 splitters by (keys,
 //                          index), so a word repeated many times is split
 //                          evenly by index
-//   auto_spl_dir_kernel    per bucket, the splitters' first-byte directory
-//   auto_partition_kernel  every word finds its segment by binary search over
-//                          the splitters (staged in shared memory) and takes a
-//                          slot with a warp-aggregated atomic; a slot past the
-//                          region's end only counts and raises the overflow flag
+//   auto_spl_dir_kernel    per bucket, the splitters' directory (two-byte
+//                          codes) and every segment's byte-code record, taken
+//                          from its two bounding splitters
+//   auto_partition_kernel  tiles of a bucket: every word finds its segment
+//                          (directory, then binary search over the splitters
+//                          staged in shared memory), counts per segment in the
+//                          tile, one reservation per (tile, segment); a slot
+//                          past the region's end only counts and raises the
+//                          overflow flag
 //   auto_layout_kernel     output base of every segment (scan of the exact
 //                          counts); on overflow, exact regions for a retry
 //   auto_partition_kernel  (again) the retry pass, a no-op unless overflow
-//   auto_segsort_kernel    one CTA per segment: bulk-copy (TMA) the segment
-//                          into shared memory, sort it (one key word: LSD
-//                          radix sort of (key - kmin, index) items held in
-//                          registers; longer keys: bitonic network in shared
-//                          memory), write the final records and permutation at
-//                          the segment's output base; a segment larger than
-//                          shared memory (only after a retry) is sorted in
-//                          chunks and merged in global memory
+//   auto_segsort_kernel    persistent CTAs take segments from a counter:
+//                          bulk-copy (TMA) the segment into shared memory,
+//                          recode one- and two-key words with the segment's
+//                          byte code, sort the (code, index) items by a
+//                          counting pass and rank placement within buckets
+//                          (overfull buckets split again in shared memory;
+//                          LSD radix passes only past the split area), sort
+//                          longer keys with a bitonic network, and write the
+//                          final records and permutation at the segment's
+//                          output base; a segment larger than shared memory
+//                          (only after a retry) is sorted in chunks and merged
+//                          in global memory
 #include <type_traits>
 
 #include "block_scan.cuh"
