@@ -130,6 +130,31 @@ def test_auto_frequent_words_split_their_buckets(env):
     assert_same_answer(out_rec, out_perm, off, expect, n)
 
 
+@pytest.mark.parametrize("L,alphabet", [(8, bytes(range(1, 256))), (12, b"abcdefghijklmnopqrstuvwxyz")])
+def test_auto_frequent_words_split_two_part_items(env, L, alphabet):
+    """As above with codes too wide for one machine word next to the index:
+    eight bytes of any value (one key word) and twelve lower-case letters (two
+    key words) make (code, index) items, whose overfull buckets split on the
+    code bits first and on the index bits once the code is shared."""
+    torch, bs, orc = env
+    n, W = 400_000, 16
+    rng = np.random.default_rng(19 + L)
+    a = np.frombuffer(alphabet, np.uint8)
+    rec = np.zeros((n, W), np.uint8)
+    rec[:, :L] = a[rng.integers(0, a.size, size=(n, L))]
+    pick = rng.random(n)
+    base = a[rng.integers(0, a.size, size=L)]
+    for k, (lo, hi) in enumerate(((0.0, 0.35), (0.35, 0.55), (0.55, 0.62))):
+        w = base.copy()
+        w[-1] = a[(k * 7) % a.size]
+        rec[(pick >= lo) & (pick < hi), :L] = w
+    ln = np.full(n, L, np.uint8)
+    expect = orc.stable_sort(orc.Words(rec, ln))
+    s, (out_rec, out_perm, off) = run(env, rec, ln)
+    assert s.status() == 0
+    assert_same_answer(out_rec, out_perm, off, expect, n)
+
+
 @pytest.mark.parametrize("L,alphabet", [(4, b"abcdefghijklmnopqrstuvwxyz"), (8, MIXED)])
 def test_auto_frequent_word_missed_by_sample_overfills_a_bucket(env, L, alphabet):
     """4,000 copies of one word, all at positions the stratified sample skips,
