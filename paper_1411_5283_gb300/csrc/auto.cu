@@ -755,6 +755,55 @@ auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoV
   }
 }
 
+// ---- one-key segments: byte recoding -----------------------------------
+// A one-key segment's keys (big-endian, bytes past the word zero) are recoded
+// position by position: byte position p (0 = most significant) maps value b to
+// b - lo_p in a field just wide enough for the segment's range at p, and the
+// fields are laid out most significant first.  The code orders like the key
+// (the byte order is kept within every field and the fields follow the byte
+// positions) and decodes back exactly.  A segment's ranges come from its
+// bounding splitters: positions before p0 (where the splitters first differ)
+// are constant and take no bits, position p0 takes w0 bits, each of the n
+// later positions of the word wl bits (the range of all bytes inside words, 5
+// for lower-case letters), so codes are narrow and their top bits spread.
+// key - lo (lo: every position's smallest byte, packed) has no borrows, so its
+// bytes are the field values; packing byte lanes into wl-bit fields, and back,
+// takes three halving steps of masked shifts on the two 32-bit halves.
+struct ByteCode {
+  uint64_t lo;
+  uint32_t p0, w0, wl, n;  // n wl <= 56, p0 <= 7
+  __device__ __forceinline__ uint64_t encode(uint64_t key) const {
+    const uint64_t d = (key - lo) << (8 * p0);  // lane 0 (top byte): position p0
+    const uint32_t b0 = static_cast<uint32_t>(d >> 56);
+    const uint64_t t = d << 8;  // lanes 0 .. n-1: the later positions, then zeros
+    const uint32_t s1 = 8 - wl, s2 = 16 - 2 * wl;
+    uint32_t h = static_cast<uint32_t>(t >> 32), l = static_cast<uint32_t>(t);
+    h = ((h & 0xFF00FF00u) >> s1) | (h & 0x00FF00FFu);  // 16-bit groups of 2 fields
+    l = ((l & 0xFF00FF00u) >> s1) | (l & 0x00FF00FFu);
+    h = ((h & 0xFFFF0000u) >> s2) | (h & 0x0000FFFFu);  // halves of 4 fields
+    l = ((l & 0xFFFF0000u) >> s2) | (l & 0x0000FFFFu);
+    const uint64_t packed = (static_cast<uint64_t>(h) << (4 * wl)) | l;  // lanes 0..7 in 8 wl bits
+    const uint64_t tail = n ? packed >> (wl * (8 - n)) : 0ull;
+    return (static_cast<uint64_t>(b0) << (n * wl)) | tail;
+  }
+  __device__ __forceinline__ uint64_t decode(uint64_t code) const {
+    const uint32_t nt = n * wl;
+    const uint32_t b0 = static_cast<uint32_t>(code >> nt);
+    const uint64_t packed = n ? (code & ((1ull << nt) - 1)) << (wl * (8 - n)) : 0ull;
+    const uint32_t s1 = 8 - wl, s2 = 16 - 2 * wl;
+    const uint32_t m4 = wl == 8 ? 0xFFFFFFFFu : (1u << (4 * wl)) - 1u;
+    const uint32_t m2 = (1u << (2 * wl)) - 1u, m1 = ((1u << wl) - 1u) * 0x00010001u;
+    uint32_t h = static_cast<uint32_t>(packed >> (4 * wl)), l = static_cast<uint32_t>(packed) & m4;
+    h = ((h << s2) & (m2 << 16)) | (h & m2);
+    l = ((l << s2) & (m2 << 16)) | (l & m2);
+    h = ((h << s1) & (m1 << 8)) | (h & m1);
+    l = ((l << s1) & (m1 << 8)) | (l & m1);
+    const uint64_t t = (static_cast<uint64_t>(h) << 32) | l;
+    const uint64_t d = (static_cast<uint64_t>(b0) << 56) | (t >> 8);
+    return (d >> (8 * p0)) + lo;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // 3. partition
 // ---------------------------------------------------------------------------
@@ -965,6 +1014,12 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
   __syncthreads();
   const uint32_t tiles = tp[W + 1];
   const DirShape ds = dir_shape(v.hdr);
+  // A one-key segment that will be sorted in shared memory and whose item
+  // (code 2^ib + index) fits 64 bits gets its elements as that item, the code
+  // from the segment's byte-code record (staged in shared memory after the
+  // splitter table when it fits): the segment sort then copies 8 instead of
+  // 12 bytes per element and skips the encoding.
+  const uint32_t item_ib = 32u - static_cast<uint32_t>(__clz(v.hdr->imax | 1u));
   uint32_t staged = 0;  // bucket whose splitter table is in shared memory
   bool overflow = false;
   uint32_t L = 1;  // bucket of tile t (block-uniform; a CTA's tiles increase)
@@ -979,15 +1034,53 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
     const uint8_t* tab = v.spl + p.spl_off;
     const uint32_t tb = p.g > 1 ? static_cast<uint32_t>(spl_bytes_of(p.g, K)) : 0u;
     const bool tab_smem = tb <= kPartSplSmem;
-    if (tab_smem && tb && staged != L) {
+    // one-key records: lo (two words), shape, code width per segment
+    uint4* recs = reinterpret_cast<uint4*>(tabs + tb);
+    const bool rec_smem = K == 1 && tb + p.g * 16 <= kPartSplSmem;
+    if (staged != L) {
       // earlier readers of the staged table are done (barrier ending the
       // previous tile)
-      const uint4* src = reinterpret_cast<const uint4*>(tab);
-      uint4* dst = reinterpret_cast<uint4*>(tabs);
-      for (uint32_t q = threadIdx.x; q < tb / 16; q += blockDim.x) dst[q] = src[q];
+      if (tab_smem && tb) {
+        const uint4* src = reinterpret_cast<const uint4*>(tab);
+        uint4* dst = reinterpret_cast<uint4*>(tabs);
+        for (uint32_t q = threadIdx.x; q < tb / 16; q += blockDim.x) dst[q] = src[q];
+      }
+      if (rec_smem) {
+        for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) {
+          const uint32_t* f = v.segf + static_cast<size_t>(p.seg0 + q) * kSegFWords;
+          recs[q] = make_uint4(f[18], f[19], f[20], f[16]);
+        }
+      }
       staged = L;
     }
     if (tab_smem) tab = tabs;
+    const auto seg_rec = [&](uint32_t sgm) {
+      if (rec_smem) return recs[sgm];
+      const uint32_t* f = v.segf + static_cast<size_t>(p.seg0 + sgm) * kSegFWords;
+      return make_uint4(f[18], f[19], f[20], f[16]);
+    };
+    // element e of the tile to its region slot: the item of a one-key segment
+    // sorted in shared memory when it fits 64 bits, else key words and index
+    const auto put = [&](uint32_t sgm, uint32_t pos, uint32_t rc, uint64_t rb, uint64_t ib, uint64_t key0,
+                         uint32_t idx, uint32_t e) {
+      if (K == 1 && rc <= auto_seg_cap(1)) {
+        const uint4 r = seg_rec(sgm);
+        if (r.w + item_ib <= 64) {
+          ByteCode bc;
+          bc.lo = (static_cast<uint64_t>(r.x) << 32) | r.y;
+          bc.p0 = r.z & 255u;
+          bc.w0 = (r.z >> 8) & 255u;
+          bc.wl = (r.z >> 16) & 255u;
+          bc.n = r.z >> 24;
+          v.area64[rb + pos] = (bc.encode(key0) << item_ib) | idx;
+          return;
+        }
+      }
+      v.area64[rb + pos] = key0;
+      for (uint32_t k = 1; k < K; ++k)
+        v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = k0p[static_cast<uint64_t>(k) * count + e0 + e];
+      v.area32[ib + pos] = idx;
+    };
     const bool local = p.g <= kPartCounters;
     if (local)
       for (uint32_t q = threadIdx.x; q < p.g; q += blockDim.x) cnt[q] = 0;
@@ -1033,14 +1126,8 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
           rb = v.rbase[p.seg0 + sg[q]];
           ib = v.ibase[p.seg0 + sg[q]];
         }
-        if (pos < rc) {
-          v.area64[rb + pos] = key0s[q];
-          for (uint32_t k = 1; k < K; ++k)
-            v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = k0p[static_cast<uint64_t>(k) * count + e0 + e];
-          v.area32[ib + pos] = idxs[q];
-        } else {
-          overflow = true;
-        }
+        if (pos < rc) put(sg[q], pos, rc, rb, ib, key0s[q], idxs[q], e);
+        else overflow = true;
       }
     }
     if (local) {
@@ -1082,14 +1169,8 @@ auto_partition_kernel(uint32_t W, const uint32_t* __restrict__ d_off, int retry_
           rb = v.rbase[p.seg0 + s];
           ib = v.ibase[p.seg0 + s];
         }
-        if (pos < rc) {
-          v.area64[rb + pos] = key0s[q];
-          for (uint32_t k = 1; k < K; ++k)
-            v.area64[rb + static_cast<uint64_t>(k) * rc + pos] = k0p[static_cast<uint64_t>(k) * count + e0 + e];
-          v.area32[ib + pos] = idxs[q];
-        } else {
-          overflow = true;
-        }
+        if (pos < rc) put(s, pos, rc, rb, ib, key0s[q], idxs[q], e);
+        else overflow = true;
       }
     }
     __syncthreads();  // counters and staged table reused by the next tile
@@ -1290,55 +1371,6 @@ __device__ bool maybe_prefetch(uint8_t* buf, const AutoView& v, uint32_t seg, ui
   }
   return true;
 }
-
-// ---- one-key segments: byte recoding -----------------------------------
-// A one-key segment's keys (big-endian, bytes past the word zero) are recoded
-// position by position: byte position p (0 = most significant) maps value b to
-// b - lo_p in a field just wide enough for the segment's range at p, and the
-// fields are laid out most significant first.  The code orders like the key
-// (the byte order is kept within every field and the fields follow the byte
-// positions) and decodes back exactly.  A segment's ranges come from its
-// bounding splitters: positions before p0 (where the splitters first differ)
-// are constant and take no bits, position p0 takes w0 bits, each of the n
-// later positions of the word wl bits (the range of all bytes inside words, 5
-// for lower-case letters), so codes are narrow and their top bits spread.
-// key - lo (lo: every position's smallest byte, packed) has no borrows, so its
-// bytes are the field values; packing byte lanes into wl-bit fields, and back,
-// takes three halving steps of masked shifts on the two 32-bit halves.
-struct ByteCode {
-  uint64_t lo;
-  uint32_t p0, w0, wl, n;  // n wl <= 56, p0 <= 7
-  __device__ __forceinline__ uint64_t encode(uint64_t key) const {
-    const uint64_t d = (key - lo) << (8 * p0);  // lane 0 (top byte): position p0
-    const uint32_t b0 = static_cast<uint32_t>(d >> 56);
-    const uint64_t t = d << 8;  // lanes 0 .. n-1: the later positions, then zeros
-    const uint32_t s1 = 8 - wl, s2 = 16 - 2 * wl;
-    uint32_t h = static_cast<uint32_t>(t >> 32), l = static_cast<uint32_t>(t);
-    h = ((h & 0xFF00FF00u) >> s1) | (h & 0x00FF00FFu);  // 16-bit groups of 2 fields
-    l = ((l & 0xFF00FF00u) >> s1) | (l & 0x00FF00FFu);
-    h = ((h & 0xFFFF0000u) >> s2) | (h & 0x0000FFFFu);  // halves of 4 fields
-    l = ((l & 0xFFFF0000u) >> s2) | (l & 0x0000FFFFu);
-    const uint64_t packed = (static_cast<uint64_t>(h) << (4 * wl)) | l;  // lanes 0..7 in 8 wl bits
-    const uint64_t tail = n ? packed >> (wl * (8 - n)) : 0ull;
-    return (static_cast<uint64_t>(b0) << (n * wl)) | tail;
-  }
-  __device__ __forceinline__ uint64_t decode(uint64_t code) const {
-    const uint32_t nt = n * wl;
-    const uint32_t b0 = static_cast<uint32_t>(code >> nt);
-    const uint64_t packed = n ? (code & ((1ull << nt) - 1)) << (wl * (8 - n)) : 0ull;
-    const uint32_t s1 = 8 - wl, s2 = 16 - 2 * wl;
-    const uint32_t m4 = wl == 8 ? 0xFFFFFFFFu : (1u << (4 * wl)) - 1u;
-    const uint32_t m2 = (1u << (2 * wl)) - 1u, m1 = ((1u << wl) - 1u) * 0x00010001u;
-    uint32_t h = static_cast<uint32_t>(packed >> (4 * wl)), l = static_cast<uint32_t>(packed) & m4;
-    h = ((h << s2) & (m2 << 16)) | (h & m2);
-    l = ((l << s2) & (m2 << 16)) | (l & m2);
-    h = ((h << s1) & (m1 << 8)) | (h & m1);
-    l = ((l << s1) & (m1 << 8)) | (l & m1);
-    const uint64_t t = (static_cast<uint64_t>(h) << 32) | l;
-    const uint64_t d = (static_cast<uint64_t>(b0) << 56) | (t >> 8);
-    return (d >> (8 * p0)) + lo;
-  }
-};
 
 // ---- one-key segments: LSD radix sort -----------------------------------
 // A one-key segment (words of at most 8 letters) orders its elements by the
@@ -1861,8 +1893,9 @@ __device__ __noinline__ uint32_t k1_radix(uint32_t buf_off, uint32_t c, ByteCode
   uint32_t* warp_tmp = reinterpret_cast<uint32_t*>(hist + kRxWarps * kRxDigits);
   uint32_t idx_off = 0;
   if constexpr (sizeof(It) == sizeof(Item64)) {
-    auto get = [=](uint32_t p) { return Item64{(bc.encode(kp[p]) << ib) | ip[p]}; };
-    // the index plane is free once the items are in registers: bucket counters
+    // the partition wrote these segments as items (code 2^ib + index)
+    auto get = [=](uint32_t p) { return Item64{kp[p]}; };
+    // the index plane is free: bucket counters
     radix_sort_items<It, Store64, E>(get, c, kb + ib, ib, Store64{kp}, hist, warp_tmp, ip, P64{kp});
   } else {
     auto get = [=](uint32_t p) { return Item96{bc.encode(kp[p]), ip[p]}; };
