@@ -40,14 +40,14 @@ NCU_TRAFFIC = {
     # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
-    "auto_segsort": {"bytes": 4 * (55.44e6 + 126.34e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "d2a77c7e86d7",
+    "auto_segsort": {"bytes": 4 * (76.73e6 + 126.32e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "052163496737",
                                  "paper_1411_5283_gb300/csrc/common.cuh": "74c36b14a4c1"}},
-    "auto_partition": {"bytes": 4 * (57.36e6 + 8.84e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "d2a77c7e86d7",
+    "auto_partition": {"bytes": 4 * (55.02e6 + 2.41e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "052163496737",
                                    "paper_1411_5283_gb300/csrc/common.cuh": "74c36b14a4c1"}},
-    "auto_bucket": {"bytes": 4 * (138.95e6 + 26.04e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "d2a77c7e86d7",
+    "auto_bucket": {"bytes": 4 * (139.03e6 + 26.08e6),
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "052163496737",
                                 "paper_1411_5283_gb300/csrc/common.cuh": "74c36b14a4c1"}},
 }
 
@@ -152,6 +152,10 @@ def kernel_bytes(hist: np.ndarray, n: int, Wd: int, tile: int) -> dict:
     L = np.arange(hist.size)
     K = (L + 7) // 8
     elem = (8 * K + 4) * hist  # bytes of all elements of each bucket
+    # between partition and segment sort a one-key element travels as one
+    # 8-byte item (code 2^ib + index) when that fits 64 bits, as it does for
+    # every one-key segment of the large table
+    seg_elem = np.where(K == 1, 8, 8 * K + 4) * hist
     kb = {
         "hist": n,                                            # read len
         "scatter": n * (Wd + 1) + int(elem.sum()),            # read rec+len, write keys+idx
@@ -162,8 +166,8 @@ def kernel_bytes(hist: np.ndarray, n: int, Wd: int, tile: int) -> dict:
         # elements; partition reads them and writes them into segments; segsort
         # reads the segments and writes the final records + permutation
         "auto_bucket": n * (Wd + 1) + int(elem.sum()),
-        "auto_partition": 2 * int(elem.sum()),
-        "auto_segsort": int(elem.sum()) + n * (Wd + 4),
+        "auto_partition": int(elem.sum()) + int(seg_elem.sum()),
+        "auto_segsort": int(seg_elem.sum()) + n * (Wd + 4),
     }
     merge = 0
     R = tile
