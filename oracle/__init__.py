@@ -3,7 +3,7 @@
 The oracle (``bsort_oracle.cpp``) restates the paper's method (arXiv 1411.5283,
 §3 Methodology, "Pre-processing", phases 1-3; bubble sort as described in §2 and
 §3.2) as plain single-threaded C++.  This module compiles it with g++ and wraps
-its four entry points with ctypes, taking and returning numpy arrays.
+its entry points with ctypes, taking and returning numpy arrays.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It never touches the CUDA library and
@@ -50,8 +50,12 @@ def bind(path: str):
                                     u8p, u32p, u32p, u64p]
     lib.orc_stable_sort.argtypes = [u8p, u8p, ctypes.c_uint32, ctypes.c_uint32,
                                     u8p, u32p, u32p]
+    lib.orc_bubble_sort_whole.argtypes = [u8p, u8p, ctypes.c_uint32, ctypes.c_uint32,
+                                          u8p, u32p, u64p]
+    lib.orc_stable_sort_whole.argtypes = [u8p, u8p, ctypes.c_uint32, ctypes.c_uint32,
+                                          u8p, u32p]
     for f in (lib.orc_tokenize, lib.orc_split_by_length, lib.orc_bubble_sort,
-              lib.orc_stable_sort):
+              lib.orc_stable_sort, lib.orc_bubble_sort_whole, lib.orc_stable_sort_whole):
         f.restype = ctypes.c_int
     return lib
 
@@ -162,3 +166,42 @@ def sort_text(text: bytes, W: int, method: str = "bubble") -> tuple[int, Words, 
         return st, w, None
     res = bubble_sort(w) if method == "bubble" else stable_sort(w)
     return res.status, w, res
+
+
+@dataclass
+class SortedWhole:
+    """Every word in (bytes, input index) order, without length buckets."""
+    status: int
+    out_rec: np.ndarray
+    out_perm: np.ndarray
+    swaps: int | None = None
+
+
+def _sort_whole(fn: str, w: Words, with_swaps: bool) -> SortedWhole:
+    lib = _load()
+    rec = np.ascontiguousarray(w.rec, dtype=np.uint8)
+    ln = np.ascontiguousarray(w.len, dtype=np.uint8)
+    n, W = ln.size, rec.shape[1]
+    out_rec = np.zeros((max(n, 1), W), dtype=np.uint8)
+    perm = np.zeros(max(n, 1), dtype=np.uint32)
+    args = [_p(rec, ctypes.c_uint8) if n else None, _p(ln, ctypes.c_uint8) if n else None,
+            n, W, _p(out_rec, ctypes.c_uint8), _p(perm, ctypes.c_uint32)]
+    swaps = None
+    if with_swaps:
+        sw = np.zeros(1, dtype=np.uint64)
+        args.append(_p(sw, ctypes.c_uint64))
+    st = getattr(lib, fn)(*args)
+    if with_swaps:
+        swaps = int(sw[0])
+    return SortedWhole(st, out_rec[:n], perm[:n], swaps)
+
+
+def bubble_sort_whole(w: Words) -> SortedWhole:
+    """The whole file's words by bubble sort, no length sub-arrays (Table 2,
+    second row)."""
+    return _sort_whole("orc_bubble_sort_whole", w, True)
+
+
+def stable_sort_whole(w: Words) -> SortedWhole:
+    """The same answer by one stable library sort on the byte strings."""
+    return _sort_whole("orc_stable_sort_whole", w, False)

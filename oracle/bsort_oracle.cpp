@@ -11,6 +11,8 @@
 //            compare neighbours, swap when out of order, repeat passes until a
 //            pass makes no swap; n(n-1)/2 compares in the worst case).
 // The concatenation of the sub-arrays in ascending length is the answer.
+// The paper also times the whole file sorted alphabetically by bubble sort
+// without the sub-arrays (Table 2, second row); that variant is restated too.
 //
 // Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
 // load this library. It shares no code, header or constant with the CUDA path.
@@ -195,6 +197,69 @@ int orc_stable_sort(const uint8_t* rec, const uint8_t* len, uint32_t n, uint32_t
   std::vector<std::vector<uint32_t>> sub(W + 1);
   for (uint32_t id : ids) sub[len[id]].push_back(id);
   concatenate(sub, rec, W, out_rec, out_perm, off);
+  return ORC_OK;
+}
+
+// The paper's other experiment (Table 2, second row): the whole file's words
+// sorted alphabetically by bubble sort, without the length sub-arrays.  Words
+// compare as byte strings (a proper prefix first), ties by input index (the
+// bubble sort swaps only on a strict '>').  out_rec, out_perm as above; swaps
+// receives the number of exchanges.
+int orc_bubble_sort_whole(const uint8_t* rec, const uint8_t* len, uint32_t n, uint32_t W,
+                          uint8_t* out_rec, uint32_t* out_perm, uint64_t* swaps) {
+  if (W == 0 || W > 255) return ORC_E_INVALID;
+  unsigned flags = check_lengths(len, n, W);
+  if (flags) return smallest_error(flags);
+  std::vector<uint32_t> b(n);
+  for (uint32_t i = 0; i < n; ++i) b[i] = i;
+  const auto after = [&](uint32_t x, uint32_t y) {  // word x sorts after word y
+    const uint8_t* a = rec + (uint64_t)x * W;
+    const uint8_t* c = rec + (uint64_t)y * W;
+    return std::lexicographical_compare(c, c + len[y], a, a + len[x]);
+  };
+  uint64_t exchanged = 0;
+  for (uint64_t pass = 0; n > 1 && pass < (uint64_t)n - 1; ++pass) {
+    bool swapped = false;
+    for (uint64_t j = 0; j + 1 < (uint64_t)n - pass; ++j) {
+      if (after(b[j], b[j + 1])) {
+        std::swap(b[j], b[j + 1]);
+        swapped = true;
+        ++exchanged;
+      }
+    }
+    if (!swapped) break;
+  }
+  if (swaps) *swaps = exchanged;
+  for (uint32_t r = 0; r < n; ++r) {
+    if (out_rec) {
+      std::memset(out_rec + (uint64_t)r * W, 0, W);
+      std::memcpy(out_rec + (uint64_t)r * W, rec + (uint64_t)b[r] * W, len[b[r]]);
+    }
+    if (out_perm) out_perm[r] = b[r];
+  }
+  return ORC_OK;
+}
+
+// The same answer by one stable library sort on the byte strings.
+int orc_stable_sort_whole(const uint8_t* rec, const uint8_t* len, uint32_t n, uint32_t W,
+                          uint8_t* out_rec, uint32_t* out_perm) {
+  if (W == 0 || W > 255) return ORC_E_INVALID;
+  unsigned flags = check_lengths(len, n, W);
+  if (flags) return smallest_error(flags);
+  std::vector<uint32_t> ids(n);
+  for (uint32_t i = 0; i < n; ++i) ids[i] = i;
+  std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) {
+    const uint8_t* a = rec + (uint64_t)x * W;
+    const uint8_t* c = rec + (uint64_t)y * W;
+    return std::lexicographical_compare(a, a + len[x], c, c + len[y]);
+  });
+  for (uint32_t r = 0; r < n; ++r) {
+    if (out_rec) {
+      std::memset(out_rec + (uint64_t)r * W, 0, W);
+      std::memcpy(out_rec + (uint64_t)r * W, rec + (uint64_t)ids[r] * W, len[ids[r]]);
+    }
+    if (out_perm) out_perm[r] = ids[r];
+  }
   return ORC_OK;
 }
 

@@ -237,3 +237,73 @@ def test_prose_sample_bubble_equals_stable(orc):
     s = orc.stable_sort(w)
     assert np.array_equal(b.out_perm, s.out_perm)
     check_invariants(w.rec, w.len, b, 16)
+
+
+# --------------------------------------------------------------------------
+# The whole file sorted without length sub-arrays (Table 2, second row)
+# --------------------------------------------------------------------------
+
+def whole_order(rec, ln):
+    """Input indices in (byte string, index) order: Python's own sort."""
+    return sorted(range(ln.size), key=lambda i: (bytes(rec[i, :ln[i]]), i))
+
+
+def test_whole_hand_worked(orc):
+    # "b", "ab", "a", "ab": a proper prefix first, equal words in input order;
+    # bubble sort exchanges once per inversion: (b,ab) (b,a) (b,ab) (ab,a)
+    rec, ln = words_table([b"b", b"ab", b"a", b"ab"], 8)
+    b = orc.bubble_sort_whole(orc.Words(rec, ln))
+    assert b.status == 0
+    assert b.out_perm.tolist() == [2, 1, 3, 0]
+    assert b.swaps == 4
+    assert [bytes(r).rstrip(b"\0") for r in b.out_rec] == [b"a", b"ab", b"ab", b"b"]
+
+
+@pytest.mark.parametrize("seed,n,W,alpha,high", [
+    (10, 300, 8, b"ab", False), (11, 500, 16, b"abc", False), (12, 400, 32, None, False),
+    (13, 600, 8, None, True), (14, 1, 8, None, False), (15, 0, 8, None, False),
+    (16, 700, 24, b"aA", False)])
+def test_whole_matches_python_sort(orc, seed, n, W, alpha, high):
+    rec, ln = random_table(seed, n, W, alpha, high)
+    w = orc.Words(rec, ln)
+    expect = whole_order(rec, ln)
+    b = orc.bubble_sort_whole(w)
+    s = orc.stable_sort_whole(w)
+    assert b.status == 0 and s.status == 0
+    assert b.out_perm.tolist() == expect and s.out_perm.tolist() == expect
+    assert np.array_equal(b.out_rec, s.out_rec)
+    for r, i in enumerate(expect):
+        assert np.array_equal(b.out_rec[r], rec[i])
+    # one exchange per inversion of the byte strings (independent merge count)
+    assert b.swaps == inversions([bytes(rec[i, :ln[i]]) for i in range(n)])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_whole_brute_force_tiny(orc, seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(1, 8))
+    rec, ln = random_table(2000 + seed, n, 3, b"ab")
+    keys = [(bytes(rec[i, :ln[i]]), i) for i in range(n)]
+    ordered = [p for p in itertools.permutations(range(n))
+               if all(keys[p[k]] <= keys[p[k + 1]] for k in range(n - 1))]
+    assert len(ordered) == 1
+    assert orc.bubble_sort_whole(orc.Words(rec, ln)).out_perm.tolist() == list(ordered[0])
+
+
+def test_whole_reverse_sorted_swaps_and_differs_from_bucketed(orc):
+    # distinct words in descending byte order: m(m-1)/2 exchanges (§3.2 worst case)
+    m = 120
+    words = sorted({bytes([97 + (k * 7) % 26] * (1 + k % 5)) + bytes([97 + k % 26]) for k in range(400)},
+                   reverse=True)[:m]
+    rec, ln = words_table(words, 8)
+    b = orc.bubble_sort_whole(orc.Words(rec, ln))
+    assert b.swaps == m * (m - 1) // 2
+    assert b.out_perm.tolist() == list(range(m))[::-1]
+    # the length-bucketed answer puts shorter words first instead
+    assert orc.stable_sort(orc.Words(rec, ln)).out_perm.tolist() != b.out_perm.tolist()
+
+
+def test_whole_length_errors(orc):
+    rec = np.zeros((2, 8), np.uint8)
+    assert orc.bubble_sort_whole(orc.Words(rec, np.array([0, 1], np.uint8))).status == 1
+    assert orc.stable_sort_whole(orc.Words(rec, np.array([1, 9], np.uint8))).status == 2

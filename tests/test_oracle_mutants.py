@@ -29,6 +29,12 @@ MUTANTS = {
     "compare_short": ("std::memcmp(a, c, L) > 0", "std::memcmp(a, c, L - 1) > 0"),
     "stable_by_len_only": ("return std::memcmp(rec + (uint64_t)a * W, rec + (uint64_t)b * W, len[a]) < 0;",
                            "return false;"),
+    "whole_non_strict_swap": ("return std::lexicographical_compare(c, c + len[y], a, a + len[x]);",
+                              "return !std::lexicographical_compare(a, a + len[x], c, c + len[y]);"),
+    "whole_prefix_equal": ("return std::lexicographical_compare(c, c + len[y], a, a + len[x]);",
+                           "return std::memcmp(a, c, std::min(len[x], len[y])) > 0;"),
+    "whole_stable_descending": ("return std::lexicographical_compare(a, a + len[x], c, c + len[y]);",
+                                "return std::lexicographical_compare(c, c + len[y], a, a + len[x]);"),
 }
 
 
@@ -48,6 +54,12 @@ def _run_pins(orc_mod):
         pins.test_tokenize_letter_boundaries(orc_mod)
         pins.test_reverse_sorted_swaps(orc_mod)
         pins.test_identical_and_sorted_are_identity(orc_mod)
+        pins.test_whole_hand_worked(orc_mod)
+        for args in [(10, 300, 8, b"ab", False), (13, 600, 8, None, True)]:
+            pins.test_whole_matches_python_sort(orc_mod, *args)
+        for seed in range(8):
+            pins.test_whole_brute_force_tiny(orc_mod, seed)
+        pins.test_whole_reverse_sorted_swaps_and_differs_from_bucketed(orc_mod)
     except AssertionError:
         return False
     return True
