@@ -205,3 +205,18 @@ def bubble_sort_whole(w: Words) -> SortedWhole:
 def stable_sort_whole(w: Words) -> SortedWhole:
     """The same answer by one stable library sort on the byte strings."""
     return _sort_whole("orc_stable_sort_whole", w, False)
+
+
+def pack_words(out_rec: np.ndarray, lengths: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """The paper's other data structure (§3.1, "vectors of string"): the sorted
+    words as one packed byte buffer without padding, and offsets[n + 1] with
+    word r at bytes[offsets[r]:offsets[r + 1]].  out_rec holds the sorted
+    records and lengths their lengths in the same (output) order."""
+    n = int(lengths.size)
+    offsets = np.zeros(n + 1, dtype=np.uint32)
+    parts = []
+    for r in range(n):
+        L = int(lengths[r])
+        parts.append(bytes(out_rec[r, :L]))
+        offsets[r + 1] = offsets[r] + L
+    return np.frombuffer(b"".join(parts), dtype=np.uint8).copy(), offsets

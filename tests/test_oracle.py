@@ -307,3 +307,28 @@ def test_whole_length_errors(orc):
     rec = np.zeros((2, 8), np.uint8)
     assert orc.bubble_sort_whole(orc.Words(rec, np.array([0, 1], np.uint8))).status == 1
     assert orc.stable_sort_whole(orc.Words(rec, np.array([1, 9], np.uint8))).status == 2
+
+
+# --------------------------------------------------------------------------
+# Packed output ("vectors of string", §3.1)
+# --------------------------------------------------------------------------
+
+def test_pack_words_round_trip(orc):
+    rec, ln = random_table(21, 500, 16, b"abcXYZ")
+    res = orc.stable_sort(orc.Words(rec, ln))
+    out_len = ln[res.out_perm]
+    buf, offs = orc.pack_words(res.out_rec, out_len)
+    assert offs[0] == 0 and int(offs[-1]) == int(ln.sum()) == buf.size
+    assert np.all(np.diff(offs.astype(np.int64)) == out_len)
+    # unpacking and padding gives the records back
+    for r in range(ln.size):
+        word = bytes(buf[offs[r]:offs[r + 1]])
+        assert word == bytes(rec[res.out_perm[r], :ln[res.out_perm[r]]])
+        assert word + b"\0" * (16 - len(word)) == bytes(res.out_rec[r])
+
+
+def test_pack_words_hand_worked(orc):
+    rec, ln = words_table([b"bb", b"a", b"ab"], 8)
+    res = orc.stable_sort(orc.Words(rec, ln))  # length first: a, ab, bb
+    buf, offs = orc.pack_words(res.out_rec, ln[res.out_perm])
+    assert bytes(buf) == b"aabbb" and offs.tolist() == [0, 1, 3, 5]
