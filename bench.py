@@ -80,7 +80,7 @@ def parse():
                          "calls; served: Poisson requests through the continuous-batching "
                          "server; text: the 240,000-word raw text end to end")
     ap.add_argument("--lists", type=int, default=4096)
-    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: requests per second")
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (for ncu captures): no e2e, no CPU "
@@ -279,7 +279,11 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     compulsory = n * (W + 1) + n * (W + 4)
     path_gbs = compulsory / (ms * 1e-3) / 1e9
+    # the timed step's output, kept for the oracle check of the CPU-baseline leg
+    out_perm_np = s.out_perm[:n].cpu().numpy().view(np.uint32).copy()
+    out_rec_np = s.out_rec[:n].cpu().numpy()
     return {
+        "out": (out_rec_np, out_perm_np, off, len_np),
         "ms": ms, "e2e_ms": e2e_ms, "n": n, "prof": prof, "clk": clk,
         "roofline": {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -294,13 +298,20 @@ def run_ours(args, rank, world, local_rank):
     }
 
 
-def cpu_baseline(budget_s: float = 20.0):
-    """The oracle, as it stands, on bounded samples of the same workload."""
+def cpu_baseline(out=None):
+    """The oracle, as it stands, on bounded samples of the same workload.
+
+    With ``out`` (the timed step's records, permutation, offsets and the input
+    lengths) it also checks that output against the oracle: restricted to the
+    words of the first 1,048,576 indices, the output must be exactly the
+    oracle's answer on that prefix (the sort order is a strict total order,
+    so a subset of a sorted sequence is the subset sorted), and the offsets
+    must be the prefix sums of the length histogram."""
     import oracle
     from paper_1411_5283_gb300 import synth
     oracle.build()
     rec, ln = synth.large_records(SEED, 1 << 20, W)
-    out = {}
+    out_parity = None
     # the paper's method (bubble sort per length) on a 65,536-word sample
     m = 65_536
     t0 = time.perf_counter()
@@ -313,13 +324,27 @@ def cpu_baseline(budget_s: float = 20.0):
     res = oracle.stable_sort(oracle.Words(rec, ln))
     ts = time.perf_counter() - t0
     assert res.status == 0
-    out["stable"] = (rec.shape[0], ts)
-    return {"value": round(m / tb / 1e6, 6), "unit": "Mwords/s", "cores": 1, "kind": "oracle",
+    if out is not None:
+        out_rec, out_perm, off, len_all = out
+        S = rec.shape[0]
+        keep = out_perm < S
+        mism = int(np.count_nonzero(out_perm[keep] != res.out_perm))
+        rec_ok = bool(np.array_equal(out_rec[keep], res.out_rec))
+        hist = np.bincount(len_all, minlength=W + 1)[: W + 1]
+        want_off = np.concatenate([[0], np.cumsum(hist)]).astype(np.int64)
+        off_ok = bool(np.array_equal(off, want_off))
+        out_parity = {"checked_words": S, "perm_mismatches": mism, "records_equal": rec_ok,
+                      "offsets_equal": off_ok, "ok": mism == 0 and rec_ok and off_ok,
+                      "how": f"the benchmarked call's output (last step) restricted to input indices < {S:,} vs the "
+                             "oracle's stable sort of that prefix; offsets vs the length "
+                             "histogram's prefix sums"}
+    base = {"value": round(m / tb / 1e6, 6), "unit": "Mwords/s", "cores": 1, "kind": "oracle",
             "sample": f"bubble sort per length (paper's method) on the first {m:,} words of the "
                       f"workload: {tb:.2f} s; stable-sort oracle on the first "
                       f"{rec.shape[0]:,} words: {ts:.2f} s = "
                       f"{rec.shape[0] / ts / 1e6:.3f} Mwords/s",
             "stable_sort_mwords_s": round(rec.shape[0] / ts / 1e6, 4)}
+    return base, out_parity
 
 
 def run_reference(args):
@@ -424,12 +449,38 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def served_cpu_baseline(pool, Ws):
+    """The served workload's CPU-baseline leg: the oracle (stable-sort
+    formulation, one core) on every pooled payload, timed; its answers are
+    kept to check every served response."""
+    import oracle
+    oracle.build()
+    answers, words = [], 0
+    t0 = time.perf_counter()
+    for p in pool:
+        if p[0] == "text":
+            st, w, exp = oracle.sort_text(p[1], Ws, "stable")
+            words += w.n
+        else:
+            exp = oracle.stable_sort(oracle.Words(p[1], p[2]))
+            st = exp.status
+            words += int(p[2].size)
+        assert st == 0
+        answers.append(exp)
+    sec = time.perf_counter() - t0
+    base = {"value": round(words / sec / 1e6, 4), "unit": "Mwords/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"stable-sort oracle (text payloads tokenised first) on the {len(pool)} "
+                      f"pooled payloads, {words:,} words: {sec:.2f} s"}
+    return base, answers
+
+
 def run_served(args):
     """Poisson arrivals (rate x duration) of requests log-uniform in 1,024..1,048,576
-    words (10 % raw text), through the continuous-batching server (64 GB budget).
-    Payloads come from a pool of 128 generated requests (request i uses payload
-    i mod 128).  After the timed trace the pool is served once more and every
-    pooled payload of up to 200,000 words is checked against the oracle."""
+    words (10 % raw text of the same word count), through the continuous-batching
+    server (64 GB budget).  Payloads come from a pool of 128 generated requests
+    (request i uses payload i mod 128).  Every completed response is compared
+    with the oracle's answer for its payload, then released."""
     import torch
 
     import paper_1411_5283_gb300 as bs
@@ -442,53 +493,108 @@ def run_served(args):
     for i in range(P):
         m = int(sizes[i % len(sizes)])
         if is_text[i % len(sizes)]:
-            pool.append(("text", synth.prose(10_000 + i, max(1, m // 8), 12_000)))
+            pool.append(("text", synth.prose(10_000 + i, m, 12_000), m))
         else:
             pool.append(("rec",) + synth.list_words(10_000 + i, m, 50_000, Ws))
+    base, answers = served_cpu_baseline(pool, Ws)
     srv = serve.Server(Ws, 64 << 30, max_list_words=1 << 20, max_batch_lists=1024)
-    reqs = []
-    for i in range(len(t)):
-        p = pool[i % P]
+
+    def request(rid, p, arrival=0.0):
         if p[0] == "text":
-            reqs.append(serve.Request(i, arrival=float(t[i]), text=p[1]))
-        else:
-            reqs.append(serve.Request(i, arrival=float(t[i]), rec=p[1], ln=p[2]))
+            return serve.Request(rid, arrival=arrival, text=p[1], max_words=p[2])
+        return serve.Request(rid, arrival=arrival, rec=p[1], ln=p[2])
+
+    # the oracle's answers, resident on the device so every response is
+    # compared element by element without a host copy of its result
+    exp_dev = [(torch.from_numpy(a.out_rec).cuda(), torch.from_numpy(a.out_perm.view(np.int32)).cuda(),
+                a.off) for a in answers]
+    reqs = [request(i, pool[i % P], float(t[i])) for i in range(len(t))]
     # warm up the kernels on one request of each mode
-    srv.run_trace([serve.Request(-1, text=pool[0][1]) if pool[0][0] == "text" else
-                   serve.Request(-1, rec=pool[0][1], ln=pool[0][2])])
+    srv.run_trace([request(-1, pool[0]), request(-2, next(p for p in pool if p[0] == "text"))])
     srv.done.clear()
     srv.batches = 0
-    stats = srv.run_trace(reqs, release=True)
-    # correctness of the served path: the pool again, results kept, vs the oracle
-    import oracle
-    oracle.build()
-    check = [serve.Request(10_000 + i, text=p[1]) if p[0] == "text" else
-             serve.Request(10_000 + i, rec=p[1], ln=p[2]) for i, p in enumerate(pool)]
-    srv.done.clear()
-    srv.run_trace(check, release=False)
     checked = bad = 0
-    for r, p in zip(check, pool):
-        if r.n_slots > 200_000:
-            continue
-        if p[0] == "text":
-            st, _, exp = oracle.sort_text(p[1], Ws, "stable")
-        else:
-            exp = oracle.stable_sort(oracle.Words(p[1], p[2]))
-        got = srv.result(r)
-        ok = got[0] == 0 and np.array_equal(got[2], exp.out_perm) and \
-            np.array_equal(got[1], exp.out_rec) and np.array_equal(got[3], exp.off)
+
+    def on_done(r):
+        nonlocal checked, bad
+        e_rec, e_perm, e_off = exp_dev[r.rid % P]
+        n = int(e_perm.numel())
+        ok = r.status == 0 and np.array_equal(r.off, e_off) and \
+            torch.equal(srv.out_perm[r.slot:r.slot + n], e_perm) and \
+            torch.equal(srv.out_rec[r.slot:r.slot + n], e_rec)
         checked += 1
         bad += 0 if ok else 1
         srv.release(r)
+
+    stats = srv.run_trace(reqs, release=False, on_done=on_done)
     stats["oracle_checked"] = checked
     stats["oracle_mismatches"] = bad
+    stats["requests_per_batch"] = round(len(srv.done) / max(1, stats["batches"]), 3)
     line = {"metric": "served Mwords/s and p50/p99 latency", "value": round(stats["mwords_per_s"], 2),
             "unit": "Mwords/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u8",
             "data": "synthetic", "config": {"workload": f"served: Poisson {args.rate}/s for "
                                             f"{args.duration}s, sizes 1024..1048576, 10% text",
                                             "budget_gb": 64, "pool": P},
             "p50_ms": round(stats["p50_ms"], 3), "p99_ms": round(stats["p99_ms"], 3),
-            "stats": stats}
+            "stats": stats, "cpu_baseline": base,
+            "note": "every response is compared with the oracle's answer on the device as it "
+                    "completes, inside the run, so the throughput includes the checks"}
+    print(json.dumps(line), flush=True)
+
+
+def run_text(args):
+    """Raw text end to end (tokenise, bucket, sort, gather in one call): the
+    32,768-word text of seed 0 (vocabulary 4,500) and the 240,000-word text of
+    seed 1 (vocabulary 12,000), every algorithm.  These sizes are latency
+    bound, so the line reports microseconds per call beside Mwords/s."""
+    import torch
+
+    import paper_1411_5283_gb300 as bs
+    from paper_1411_5283_gb300 import synth
+    bs._lib.load()
+    Wt = 16
+    stream = torch.cuda.current_stream()
+    results = {}
+    for name, seed, nw, V in (("small", 0, 32_768, 4_500), ("medium", 1, 240_000, 12_000)):
+        text = synth.prose(seed, nw, V)
+        d_text = torch.from_numpy(np.frombuffer(text, np.uint8).copy()).cuda()
+        s = bs.Sorter(len(text) // 2 + 1, Wt)
+        for alg in ("odd_even", "merge", "auto"):
+            def step():
+                s.sort_text(d_text, alg=alg)
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            assert s.status() == 0
+            assert int(s.n_words.item()) == nw
+            bs.bsort_profile_reset()
+            bs.bsort_profile_enable(True)
+            step()
+            torch.cuda.synchronize()
+            bs.bsort_profile_enable(False)
+            prof = bs.bsort_profile_read()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            results[f"{name}/{alg}"] = {
+                "words": nw, "text_bytes": len(text), "us_per_call": round(ms * 1e3, 2),
+                "mwords_per_s": round(nw / ms / 1e3, 2),
+                "launches_per_call": int(sum(v[0] for v in prof.values())),
+                "kernels_us": {k: round(v[1] * 1e3, 2) for k, v in prof.items()}}
+    head = results["medium/odd_even"]
+    line = {"metric": "Mwords/s sorted end-to-end from raw text (tokenise/bucket/sort/gather)",
+            "value": head["mwords_per_s"], "unit": "Mwords/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(head["us_per_call"] / 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "text: 240,000-word prose (seed 1, V=12,000), W=16, "
+                                   "odd_even; also 32,768 words (seed 0) and every algorithm",
+                       "l2": "inputs smaller than L2: latency-bound, no flush"},
+            "runs": results}
     print(json.dumps(line), flush=True)
 
 
@@ -496,6 +602,8 @@ def main():
     args = parse()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "text":
+        return run_text(args)
     if args.workload == "served":
         return run_served(args)
     rank = int(os.environ.get("RANK", 0))
@@ -531,7 +639,10 @@ def main():
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in r["prof"].items()},
             "clocks": r["clk"],
         }
-        line["cpu_baseline"] = cpu_baseline() if world == 1 else None
+        if world == 1:
+            line["cpu_baseline"], line["parity"] = cpu_baseline(r["out"])
+        else:
+            line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

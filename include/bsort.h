@@ -177,7 +177,8 @@ bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W
  *    (with the optional profiler off, its default).
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
- *    stream capture.
+ *    stream capture.  The address is kept with the id of the context it was
+ *    taken in; after cudaDeviceReset the next call looks it up again.
  *  - Every call shares the array and finds the previous call's contents; the
  *    call clears what must start at zero.  Calls that overlap on the GPU (other
  *    streams or host threads) race on the array: serialise them.
@@ -237,6 +238,20 @@ bsort_status bsort_get_status(const void* d_ws, cudaStream_t s);
 
 /* Clears the workspace status word (asynchronously on s). */
 bsort_status bsort_reset_status(void* d_ws, cudaStream_t s);
+
+/* Bound of the kernels' device-side waits, for testing the timeout path
+ * (the paper has no counterpart).  Every kernel that stages data with the
+ * bulk-copy engine waits for the copy on an mbarrier, polling at most `polls`
+ * times before it records BSORT_E_TIMEOUT and returns; the wait that then
+ * lets the copy in flight land before the CTA exits always keeps the default
+ * bound, so no copy outlives its CTA.  polls = 0 makes every such first wait
+ * give up at once (the call then reports BSORT_E_TIMEOUT and leaves its
+ * outputs undefined, and the context stays usable); BSORT_WAIT_DEFAULT
+ * restores the default of 2^26 polls.  Process-wide; read when a call is
+ * issued, so it does not change calls already queued or captured in a graph.
+ * Not thread-safe against concurrent calls that rely on the default. */
+#define BSORT_WAIT_DEFAULT 0xFFFFFFFFu
+bsort_status bsort_set_wait_limit(uint32_t polls);
 
 /* Human-readable name of a status code. */
 const char* bsort_status_string(bsort_status st);

@@ -75,6 +75,7 @@ _SIGS = {
     "bsort_profile_read": (ctypes.c_uint32, [ctypes.c_char_p, c_size,
                                              ctypes.POINTER(ctypes.c_uint64),
                                              ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
+    "bsort_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32]),
     "bsort_get_status": (ctypes.c_int, [c_u8p, c_u8p]),
     "bsort_reset_status": (ctypes.c_int, [c_u8p, c_u8p]),
     "bsort_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -246,6 +247,15 @@ def bsort_profile_read() -> dict:
     n = lib.bsort_profile_read(names, 64 * cap, launches, ms, cap)
     parts = names.raw.split(b"\0")
     return {parts[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, cap))}
+
+
+WAIT_DEFAULT = 0xFFFFFFFF
+
+
+def bsort_set_wait_limit(polls: int):
+    """Polls of the kernels' first wait for a bulk copy (WAIT_DEFAULT restores
+    the default; 0 makes every such wait give up at once)."""
+    _check(load().bsort_set_wait_limit(int(polls)), "bsort_set_wait_limit")
 
 
 def bsort_get_status(ws, stream=None) -> int:

@@ -8,6 +8,16 @@
 
 using namespace bsort;
 
+namespace bsort {
+
+namespace {
+std::atomic<uint32_t> g_first_wait_polls{kSpinLimit};
+}  // namespace
+
+uint32_t first_wait_polls() { return g_first_wait_polls.load(std::memory_order_relaxed); }
+
+}  // namespace bsort
+
 namespace {
 
 bool valid_W(uint32_t W) { return W >= 8 && W <= kMaxW && W % 8 == 0; }
@@ -79,6 +89,12 @@ bsort_status bsort_get_status(const void* d_ws, cudaStream_t s) {
   if (cudaStreamSynchronize(s) != cudaSuccess) return BSORT_E_CUDA;
   for (int c = 1; c < 32; ++c)
     if (flags & (1u << c)) return static_cast<bsort_status>(c);
+  return BSORT_OK;
+}
+
+bsort_status bsort_set_wait_limit(uint32_t polls) {
+  g_first_wait_polls.store(polls == BSORT_WAIT_DEFAULT ? kSpinLimit : polls,
+                           std::memory_order_relaxed);
   return BSORT_OK;
 }
 

@@ -2143,7 +2143,7 @@ auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_re
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) maybe_prefetch(buf, v, seg, G);
-    const bool ok = mbar_wait_bounded(bar, phase);
+    const bool ok = mbar_wait_bounded(bar, phase, ws.wait_polls);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) {
       if (threadIdx.x == 0) {
@@ -2284,14 +2284,12 @@ static_assert(2 * P64::kScratch + kMsd2Buckets <= kMsdAreaWords && 3 * P96::kScr
 // a few scalars; ptxas -v reports it) + 1 KB reserved each
 static_assert(2 * (segsort_smem_bytes() + 256 + 1024) <= 228 * 1024, "two segsort CTAs must fit an SM");
 
-int g_sm_count = 0;
-
 cudaError_t partition(uint32_t W, const uint32_t* d_off, const Ws& ws, const AutoView& v, int retry,
                       cudaStream_t s) {
-  static size_t set = 0;
+  static SmemOptIn set;
   cudaError_t e = ensure_smem(auto_partition_kernel, kPartSmem, &set);
   if (e != cudaSuccess) return e;
-  const uint32_t grid = static_cast<uint32_t>(g_sm_count);
+  const uint32_t grid = static_cast<uint32_t>(device_sm_count());
   BSORT_LAUNCH(retry ? "auto_partition_retry" : "auto_partition", auto_partition_kernel, grid,
                kPartThreads2, kPartSmem, s, W, d_off, retry, ws, v);
   return cudaGetLastError();
@@ -2309,24 +2307,19 @@ bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W) {
 cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
                         uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {
-  static size_t split_set = 0, select_set = 0, seg_set = 0;
+  static SmemOptIn split_set, select_set, seg_set;
   cudaError_t e = ensure_smem(auto_spl_sort_kernel, kSplSortSmem, &split_set);
   if (e == cudaSuccess) e = ensure_smem(auto_spl_select_kernel, kSplSelectSmem, &select_set);
   if (e == cudaSuccess) e = ensure_smem(auto_segsort_kernel, segsort_smem_bytes(), &seg_set);
   if (e != cudaSuccess) return e;
-  if (g_sm_count == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sm_count <= 0) g_sm_count = 148;
-  }
+  const int sms = device_sm_count();
   const uint32_t samples = n_cap / kAutoSampleEvery + 1;
   // the workspace view, computed once here and passed to every kernel
   const AutoView v = auto_view(ws, W);
   // phase 2 counts: totals per length, then bucket offsets
   e = cudaMemsetAsync(v.hdr->total, 0, sizeof(v.hdr->total), s);
   if (e != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_hist", auto_hist_kernel, static_cast<uint32_t>(g_sm_count) * 4, kHistThreads,
+  BSORT_LAUNCH("auto_hist", auto_hist_kernel, static_cast<uint32_t>(sms) * 4, kHistThreads,
                0, s, len, n_cap, d_n, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_offsets", auto_offsets_kernel, 1, 64, 0, s, W, ws, v, d_off);
@@ -2334,7 +2327,7 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   BSORT_LAUNCH("auto_sample", auto_sample_kernel, (samples + 255) / 256, 256, 0, s, rec, len,
                n_cap, d_n, W, d_off, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_bucket", auto_bucket_kernel, static_cast<uint32_t>(g_sm_count) * 2, kBucketThreads,
+  BSORT_LAUNCH("auto_bucket", auto_bucket_kernel, static_cast<uint32_t>(sms) * 2, kBucketThreads,
                0, s, rec, len, n_cap, d_n, W, d_off, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, s,
@@ -2351,7 +2344,7 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = partition(W, d_off, ws, v, 1, s);
   if (e != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_segsort", auto_segsort_kernel, static_cast<uint32_t>(g_sm_count) * 2,
+  BSORT_LAUNCH("auto_segsort", auto_segsort_kernel, static_cast<uint32_t>(sms) * 2,
                kSegThreads, segsort_smem_bytes(), s, W, ws, v, out_rec, out_perm);
   return cudaGetLastError();
 }

@@ -1,6 +1,7 @@
 // Shared device helpers and the workspace layout of the bsort library.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -150,6 +151,10 @@ inline uint64_t ws_capacity(size_t ws_bytes, uint32_t W) {
   return cap > 64 ? cap - 64 : 0;
 }
 
+// Polls of the first wait for a bulk copy before it gives up (host side; set
+// by bsort_set_wait_limit, read when a call is issued).
+uint32_t first_wait_polls();
+
 // Device-side view of the workspace.
 struct Ws {
   WsHeader* hdr;
@@ -159,6 +164,7 @@ struct Ws {
   uint32_t* idx[2];
   uint64_t cap;
   uint32_t K;
+  uint32_t wait_polls;  // bound of the first wait for a bulk copy (drains use kSpinLimit)
 };
 
 inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
@@ -174,19 +180,50 @@ inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
   w.autoa = reinterpret_cast<uint8_t*>(b + l.autoa);
   w.cap = l.cap;
   w.K = l.K;
+  w.wait_polls = first_wait_polls();
   return w;
 }
 
-// Raises a kernel's dynamic shared-memory limit to at least `bytes` (host).
-// `current` remembers the limit already set for that kernel.
+// Devices a process may drive; per-device host caches hold this many entries.
+constexpr int kMaxDevices = 64;
+
+// The dynamic shared-memory limit already set for one kernel, per device.
+// cudaFuncSetAttribute acts on the current device only, so a process that
+// launches on several devices must opt in on each; the entries are atomics,
+// so host threads may launch concurrently.  Static storage starts at zero.
+struct SmemOptIn {
+  std::atomic<size_t> cur[kMaxDevices];
+};
+
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (host).
 template <typename Kernel>
-inline cudaError_t ensure_smem(Kernel k, size_t bytes, size_t* current) {
+inline cudaError_t ensure_smem(Kernel k, size_t bytes, SmemOptIn* o) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   // always opt in: static shared memory counts against the 48 KB default too
-  if (bytes <= *current) return cudaSuccess;
-  const cudaError_t e =
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-  if (e == cudaSuccess) *current = bytes;
-  return e;
+  if (bytes <= o->cur[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  size_t c = o->cur[dev].load(std::memory_order_relaxed);
+  while (c < bytes && !o->cur[dev].compare_exchange_weak(c, bytes, std::memory_order_release)) {
+  }
+  return cudaSuccess;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+inline int device_sm_count() {
+  static std::atomic<int> sms[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
+  int n = sms[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 148;
+  sms[dev].store(n, std::memory_order_relaxed);
+  return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -324,9 +361,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for phase `parity` of the barrier; gives up after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+// Waits for phase `parity` of the barrier; gives up after `polls` polls
+// (kSpinLimit by default; 0 gives up at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t polls = kSpinLimit) {
+  for (uint32_t it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -29,24 +29,56 @@ constexpr size_t kNoAllocBytes = ws_layout(kNoAllocMaxWords, kMaxW).total;
 
 __device__ __align__(256) uint8_t g_noalloc_ws[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 
-// Device address of g_noalloc_ws on the current device (set up once per
-// device).  In host code the array's name is only a host-side stand-in, so the
-// address must come from cudaGetSymbolAddress with that device current.
+// Unique id of the calling thread's current CUDA context (0 if there is none
+// or the driver cannot say).  The driver functions are reached through the
+// runtime's entry-point query, so the library needs no link to the driver.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {  // called with g_mu held
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    resolved = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_noalloc_ws on the current device, set up once per
+// device and context.  In host code the array's name is only a host-side
+// stand-in, so the address must come from cudaGetSymbolAddress with that
+// device current.  The address belongs to the context the module was loaded
+// in: after cudaDeviceReset the device gets a new primary context (with a new
+// id), and the address is looked up again instead of reusing a stale one.
 cudaError_t noalloc_ptr(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_dev_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_dev_ptr[dev] || ctx == 0 || ctx != g_ctx_id[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    e = cudaGetSymbolAddress(&p, g_noalloc_ws);  // also makes the context current
     if (e != cudaSuccess) return e;
     g_dev_ptr[dev] = p;
+    g_ctx_id[dev] = current_context_id();
   }
   *out = g_dev_ptr[dev];
   return cudaSuccess;

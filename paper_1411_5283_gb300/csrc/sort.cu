@@ -105,7 +105,7 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   const uint32_t KW = W / 8;
   const uint32_t T = p.tile;
   const size_t tsm = tile_smem_bytes(KW, T);
-  static size_t tile_smem_set = 0, merge_smem_set = 0;
+  static SmemOptIn tile_smem_set, merge_smem_set;
   const uint32_t part = p.part;
   const size_t msm = merge_smem_bytes(KW, part);
   cudaError_t e = ensure_smem(tile_sort_kernel, tsm, &tile_smem_set);

@@ -152,7 +152,7 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
       bulk_g2s(kplane + j * (T + 2), ws.keys[0] + j * ws.cap + ks, kbytes, bar);
     bulk_g2s(iplane, ws.idx[0] + is, ibytes, bar);
   }
-  const bool ok = mbar_wait_bounded(bar, 0);
+  const bool ok = mbar_wait_bounded(bar, 0, ws.wait_polls);
   if (!__syncthreads_and(ok)) {
     if (threadIdx.x == 0) {
       set_error(ws.hdr, BSORT_E_TIMEOUT);

@@ -136,6 +136,7 @@ Many many_view(void* base, size_t ws_bytes, uint32_t W, uint32_t n_lists, const 
   m.table = reinterpret_cast<uint32_t*>(b + l.table);
   m.trec = reinterpret_cast<uint8_t*>(b + l.trec);
   m.tlen = reinterpret_cast<uint8_t*>(b + l.tlen);
+  m.ws.wait_polls = first_wait_polls();
   m.ws.hdr = reinterpret_cast<WsHeader*>(b + l.header + 256);
   m.ws.table = m.table;
   m.ws.autoa = nullptr;
@@ -531,7 +532,6 @@ __global__ void many_finish_kernel(Many m, int32_t* __restrict__ status) {
   }
 }
 
-int g_many_sms = 0;
 
 }  // namespace
 
@@ -549,22 +549,17 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
                         const SortParams& p, uint32_t* out_off, uint8_t* out_rec,
                         uint32_t* out_perm, int32_t* list_status, void* d_ws, size_t ws_bytes,
                         cudaStream_t s) {
-  if (g_many_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_many_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_many_sms <= 0) g_many_sms = 148;
-  }
+  const int sms = device_sm_count();
   Many m = many_view(d_ws, ws_bytes, W, n_lists, lists);
   m.T = p.tile;
   m.part = p.part;
   const uint32_t KW = W / 8;
   const size_t tsm = tile_smem_bytes(KW, p.tile), msm = merge_smem_bytes(KW, p.part);
-  static size_t tile_set = 0, merge_set = 0;
+  static SmemOptIn tile_set, merge_set;
   cudaError_t e = ensure_smem(many_tile_kernel, tsm, &tile_set);
   if (e == cudaSuccess) e = ensure_smem(many_merge_kernel, msm, &merge_set);
   if (e != cudaSuccess) return e;
-  const uint32_t grid = static_cast<uint32_t>(g_many_sms) * 4;
+  const uint32_t grid = static_cast<uint32_t>(sms) * 4;
   BSORT_LAUNCH("many_init", many_init_kernel, 1, 1024, 0, s, m, text);
   if (text) BSORT_LAUNCH("many_tokenize", many_tok_kernel, grid, kTokThreads, 0, s, text_or_rec, m);
   BSORT_LAUNCH("many_plan", many_plan_kernel, 1, 1024, 0, s, m, max_list_words);

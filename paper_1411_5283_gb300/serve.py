@@ -35,8 +35,8 @@ class Request:
     """One sort request: a word table (rec [n, W], len [n]) or a raw text."""
     rid: int
     arrival: float = 0.0                     # seconds after the loop started
-    rec: np.ndarray | None = None
-    ln: np.ndarray | None = None
+    rec: object = None                       # numpy array, or a (pinned) CPU tensor
+    ln: object = None
     text: bytes | None = None
     max_words: int | None = None             # text mode: word slots to reserve
     # filled by the server
@@ -49,6 +49,8 @@ class Request:
     text_off: int = -1
     off: np.ndarray | None = None
     cancelled: bool = False
+    ev_start: object = None                  # CUDA events around the request's batch
+    ev_end: object = None
 
     @property
     def is_text(self) -> bool:
@@ -58,7 +60,7 @@ class Request:
     def n_slots(self) -> int:
         if self.is_text:
             return self.max_words if self.max_words is not None else len(self.text) // 2 + 1
-        return int(self.ln.size)
+        return int(self.ln.shape[0])
 
     @property
     def latency(self) -> float:
@@ -98,6 +100,82 @@ class RangeAllocator:
     @property
     def free_total(self) -> int:
         return sum(l for _, l in self.free)
+
+
+class Admission:
+    """Admission by free device memory (host bookkeeping only, no GPU).
+
+    Requests wait first in, first out until their word slots (and text bytes)
+    fit the free part of the arenas; a request larger than an arena, or than
+    the batched call's per-list limit, is rejected with ``BSORT_E_NOMEM``."""
+
+    def __init__(self, n_slots: int, text_bytes: int, max_list_words: int):
+        self.n_slots, self.max_list_words = n_slots, max_list_words
+        self.slots = RangeAllocator(n_slots, align=16)
+        self.texts = RangeAllocator(max(text_bytes, 16), align=16)
+        self.waiting: deque[Request] = deque()
+        self.admitted: list[Request] = []
+        self.rejected: list[Request] = []
+
+    def _reject(self, req: Request, now: float):
+        req.status = _lib.E_NOMEM
+        req.t_done = now
+        self.rejected.append(req)
+
+    def submit(self, req: Request, now: float):
+        """Queues a request (it is admitted as soon as memory allows)."""
+        if req.n_slots > self.n_slots or (req.is_text and len(req.text) > self.texts.size) \
+                or req.n_slots > self.max_list_words:
+            self._reject(req, now)
+            return
+        self.waiting.append(req)
+
+    def cancel(self, req: Request) -> bool:
+        """Cancels a request not yet launched; returns whether it was."""
+        if req in self.waiting:
+            self.waiting.remove(req)
+        elif req in self.admitted:
+            self.admitted.remove(req)
+            self.release(req)
+        else:
+            return False
+        req.cancelled = True
+        return True
+
+    def admit(self, now: float):
+        while self.waiting:
+            req = self.waiting[0]
+            slot = self.slots.alloc(req.n_slots)
+            if slot < 0:
+                return  # first in, first out: wait for memory
+            toff = -1
+            if req.is_text:
+                toff = self.texts.alloc(max(1, len(req.text)))
+                if toff < 0:
+                    self.slots.release(slot, req.n_slots)
+                    return
+            self.waiting.popleft()
+            req.slot, req.slots, req.text_off = slot, req.n_slots, toff
+            req.t_admit = now
+            self.admitted.append(req)
+
+    def unblock(self, in_flight: bool, now: float):
+        """With nothing admitted and nothing in flight, the head request waits
+        for memory that only completed requests still hold (their results are
+        kept): nothing will ever free it.  It is rejected with
+        ``BSORT_E_NOMEM`` instead of waiting forever, and admission goes on
+        with the next request."""
+        while self.waiting and not self.admitted and not in_flight:
+            self._reject(self.waiting.popleft(), now)
+            self.admit(now)
+
+    def release(self, req: Request):
+        if req.slot >= 0:
+            self.slots.release(req.slot, req.slots)
+            req.slot = -1
+        if req.text_off >= 0:
+            self.texts.release(req.text_off, max(1, len(req.text)))
+            req.text_off = -1
 
 
 @dataclass
@@ -153,8 +231,8 @@ class Server:
         self.out_rec = torch.empty((S, W), dtype=torch.uint8, device=device)
         self.out_perm = torch.empty(S, dtype=torch.int32, device=device)
         self.text = torch.empty(max(text_bytes, 16), dtype=torch.uint8, device=device)
-        self.slots = RangeAllocator(S, align=16)
-        self.texts = RangeAllocator(max(text_bytes, 16), align=16)
+        self.adm = Admission(S, text_bytes, max_list_words)
+        self.slots, self.texts = self.adm.slots, self.adm.texts
         self.lanes = []
         for _ in range(n_streams):
             ws_bytes = _lib.bsort_sort_many_workspace_size(S, max_batch_lists, W)
@@ -169,10 +247,9 @@ class Server:
                 status_host=torch.empty(max_batch_lists, dtype=torch.int32).pin_memory(),
                 off_dev=torch.empty((max_batch_lists, W + 2), dtype=torch.int32, device=device),
                 off_host=torch.empty((max_batch_lists, W + 2), dtype=torch.int32).pin_memory()))
-        self.waiting: deque[Request] = deque()
-        self.admitted: list[Request] = []
+        self.waiting, self.admitted, self.rejected = (self.adm.waiting, self.adm.admitted,
+                                                      self.adm.rejected)
         self.done: list[Request] = []
-        self.rejected: list[Request] = []
         self.batches = 0
         self.t0 = time.perf_counter()
 
@@ -183,50 +260,17 @@ class Server:
     # -- admission --------------------------------------------------------------
     def submit(self, req: Request):
         """Queues a request (it is admitted as soon as memory allows)."""
-        if req.n_slots > self.n_slots or (req.is_text and len(req.text) > self.texts.size) \
-                or req.n_slots > self.max_list_words:
-            req.status = _lib.E_NOMEM
-            req.t_done = self.now()
-            self.rejected.append(req)
-            return
-        self.waiting.append(req)
+        self.adm.submit(req, self.now())
 
     def cancel(self, req: Request) -> bool:
         """Cancels a request not yet launched; returns whether it was."""
-        if req in self.waiting:
-            self.waiting.remove(req)
-        elif req in self.admitted:
-            self.admitted.remove(req)
-            self._release(req)
-        else:
-            return False
-        req.cancelled = True
-        return True
+        return self.adm.cancel(req)
 
     def _admit(self):
-        while self.waiting:
-            req = self.waiting[0]
-            slot = self.slots.alloc(req.n_slots)
-            if slot < 0:
-                return  # first in, first out: wait for memory
-            toff = -1
-            if req.is_text:
-                toff = self.texts.alloc(max(1, len(req.text)))
-                if toff < 0:
-                    self.slots.release(slot, req.n_slots)
-                    return
-            self.waiting.popleft()
-            req.slot, req.slots, req.text_off = slot, req.n_slots, toff
-            req.t_admit = self.now()
-            self.admitted.append(req)
+        self.adm.admit(self.now())
 
     def _release(self, req: Request):
-        if req.slot >= 0:
-            self.slots.release(req.slot, req.slots)
-            req.slot = -1
-        if req.text_off >= 0:
-            self.texts.release(req.text_off, max(1, len(req.text)))
-            req.text_off = -1
+        self.adm.release(req)
 
     # -- batches ----------------------------------------------------------------
     def _launch(self, lane: _Lane):
@@ -246,10 +290,14 @@ class Server:
                         src = torch.frombuffer(bytearray(r.text), dtype=torch.uint8)
                         self.text[r.text_off:r.text_off + len(r.text)].copy_(src, non_blocking=True)
                 else:
-                    self.in_rec[r.slot:r.slot + r.slots].copy_(torch.from_numpy(r.rec),
-                                                               non_blocking=True)
-                    self.in_len[r.slot:r.slot + r.slots].copy_(torch.from_numpy(r.ln),
-                                                               non_blocking=True)
+                    # a pinned CPU tensor is copied asynchronously; a numpy
+                    # array is staged by the driver first
+                    rec = r.rec if torch.is_tensor(r.rec) else torch.from_numpy(r.rec)
+                    ln = r.ln if torch.is_tensor(r.ln) else torch.from_numpy(r.ln)
+                    self.in_rec[r.slot:r.slot + r.slots].copy_(rec, non_blocking=True)
+                    self.in_len[r.slot:r.slot + r.slots].copy_(ln, non_blocking=True)
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(lane.stream)
             # one call per mode; lists of a mode take consecutive descriptor rows
             order = [r for r in batch if not r.is_text] + [r for r in batch if r.is_text]
             desc = np.zeros(len(order), dtype=LIST_DTYPE)
@@ -280,8 +328,10 @@ class Server:
                                      lane.status_dev[n_rec:], lane.ws, lane.ws_bytes, sp)
             lane.status_host[:len(order)].copy_(lane.status_dev[:len(order)], non_blocking=True)
             lane.off_host[:len(order)].copy_(lane.off_dev[:len(order)], non_blocking=True)
-            lane.event = torch.cuda.Event()
+            lane.event = torch.cuda.Event(enable_timing=True)
             lane.event.record(lane.stream)
+        for r in order:
+            r.ev_start, r.ev_end = start, lane.event
         lane.batch = order
         self.batches += 1
 
@@ -305,6 +355,7 @@ class Server:
             if lane.event is not None and lane.event.query():
                 self._complete(lane, release)
         self._admit()
+        self.adm.unblock(any(l.event is not None for l in self.lanes), self.now())
         for lane in self.lanes:
             if lane.event is None and self.admitted:
                 self._launch(lane)

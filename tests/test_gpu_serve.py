@@ -104,3 +104,33 @@ def test_cancel_and_malformed(env):
     st, res = expected(orc, a)
     got = srv.result(a)
     assert np.array_equal(got[2], res.out_perm)
+
+
+def test_two_batches_overlap_on_the_device(env):
+    """Two large requests arriving together go to the two lanes as two
+    batches; the CUDA events around each batch show the second starting on
+    the device before the first has finished (inputs come from pinned host
+    memory, so both launches are queued at once)."""
+    torch, serve, orc = env
+    srv = serve.Server(W, 1 << 30, max_list_words=1 << 20, max_batch_lists=1)
+    reqs, want = [], []
+    for i in range(2):
+        rec, ln = synth.list_words(3000 + i, 1_000_000, 50_000, W)
+        want.append(orc.stable_sort(orc.Words(rec, ln)))
+        reqs.append(serve.Request(i, arrival=0.0, rec=torch.from_numpy(rec).pin_memory(),
+                                  ln=torch.from_numpy(ln).pin_memory()))
+    ref = torch.cuda.Event(enable_timing=True)
+    ref.record()
+    torch.cuda.synchronize()
+    stats = srv.run_trace(reqs, release=False)
+    assert stats["completed"] == 2 and stats["batches"] == 2
+    a, b = reqs
+    assert a.ev_start is not b.ev_start
+    a0, a1 = ref.elapsed_time(a.ev_start), ref.elapsed_time(a.ev_end)
+    b0, b1 = ref.elapsed_time(b.ev_start), ref.elapsed_time(b.ev_end)
+    assert min(a1, b1) > max(a0, b0), f"batches did not overlap: {(a0, a1)} vs {(b0, b1)}"
+    for r, res in zip(reqs, want):
+        got = srv.result(r)
+        assert got[0] == 0
+        assert np.array_equal(got[2], res.out_perm)
+        assert np.array_equal(got[1], res.out_rec)
