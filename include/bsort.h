@@ -162,6 +162,50 @@ bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W
                              uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
                              uint32_t* d_off, void* d_ws, size_t ws_bytes, cudaStream_t s);
 
+/* The paper's unbucketed variant (Table 2, second row: the whole file sorted
+ * alphabetically by bubble sort, without the length sub-arrays), on a word
+ * table: every word ordered by its bytes as an unsigned byte string, a proper
+ * prefix before the longer word ("a" < "a\0" < "ab"), equal words in input
+ * order.  d_out_rec[n*W] receives the sorted records (zero padded) and
+ * d_out_perm[n] the input index of each output word.  alg picks the sort of
+ * the length buckets the call goes through first (the order inside a bucket
+ * is the same in both variants); the sorted buckets are then merged in
+ * ceil(log2 W) stable merge levels, equal records taking the shorter length
+ * first.  The bucket offsets stay inside the workspace.  Same workspace,
+ * alignment and device errors as bsort_sort_records; resets the status word
+ * first. */
+bsort_status bsort_sort_records_whole(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                      uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                      uint8_t* d_out_rec, uint32_t* d_out_perm, void* d_ws,
+                                      size_t ws_bytes, cudaStream_t s);
+
+/* The unbucketed variant on raw text (phase 1 of §3, then the order of
+ * bsort_sort_records_whole); arguments as bsort_sort_text without d_off. */
+bsort_status bsort_sort_text_whole(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                                   uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                                   uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                                   uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                                   void* d_ws, size_t ws_bytes, cudaStream_t s);
+
+/* The paper's other data structure for the words (§3.1, "vectors of
+ * string", against the fixed-width 3-D char array of the abstract): the n
+ * sorted words of d_rec[n*W] (records in output order, as written by the
+ * calls above) packed back to back without padding into d_bytes, word r at
+ * d_bytes[d_offsets[r] .. d_offsets[r+1]-1], d_offsets[n] = total bytes.
+ * Word r's length: with d_off (the W + 2 bucket offsets of a bucketed call)
+ * the L with off[L] <= r < off[L+1], and n is then min(n, off[W+1]), so the
+ * device-side word count of the text path applies; with d_off NULL it is
+ * d_len[d_perm[r]] (input lengths through the permutation; any order, e.g.
+ * the unbucketed one).  bytes_cap is the capacity of d_bytes: a larger total
+ * records BSORT_E_CAPACITY in the workspace status, writes no bytes and sets
+ * d_offsets[n] = 0.  n must be at most 2^28 words and n W below
+ * 2^32 (else BSORT_E_CAPACITY).  The workspace (any size valid for W) holds
+ * per-tile sums. */
+bsort_status bsort_pack_words(uint32_t n, uint32_t W, const uint8_t* d_rec, const uint32_t* d_off,
+                              const uint32_t* d_perm, const uint8_t* d_len, uint8_t* d_bytes,
+                              uint64_t bytes_cap, uint32_t* d_offsets, void* d_ws,
+                              size_t ws_bytes, cudaStream_t s);
+
 /* The paper has no counterpart to this entry point.
  * bsort_sort_records without a workspace, for callers that may not allocate
  * device memory: code whose device memory belongs to a host framework's own

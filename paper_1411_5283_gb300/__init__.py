@@ -10,9 +10,10 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (ALGS, AUTO, MERGE, ODD_EVEN, BsortError, ListDesc, Tune,  # noqa: F401
                    bsort_bucket_by_length, bsort_export_buckets, bsort_gather,
-                   bsort_get_status, bsort_profile_enable, bsort_profile_read,
+                   bsort_get_status, bsort_pack_words, bsort_profile_enable, bsort_profile_read,
                    bsort_profile_reset, bsort_reset_status, bsort_sort_buckets, bsort_sort_many,
-                   bsort_sort_many_workspace_size, bsort_sort_records, bsort_sort_text,
+                   bsort_sort_many_workspace_size, bsort_sort_records, bsort_sort_records_whole,
+                   bsort_sort_text, bsort_sort_text_whole,
                    bsort_status_string, bsort_tokenize, bsort_workspace_capacity, bsort_workspace_init,
                    bsort_workspace_size)
 
@@ -84,16 +85,51 @@ class Sorter:
                            self.ws, self.ws_bytes)
         return self.out_rec[:n], self.out_perm[:n], self.off
 
-    def sort_text(self, text, alg="auto", tune=None, max_words: int | None = None):
-        """Phases 1-3 on raw text; returns (out_rec, out_perm, off, n_words device tensor,
-        rec, len, src_off).  Outputs past n_words are unspecified."""
-        torch = self.torch
+    def sort_records_whole(self, rec, ln, n: int | None = None, alg="auto", tune=None):
+        """The unbucketed order (bytes, a proper prefix first, then input
+        index) on a word table; returns (out_rec, out_perm)."""
+        n = int(ln.numel()) if n is None else n
+        bsort_sort_records_whole(rec, ln, n, self.W, alg, tune, self.out_rec, self.out_perm,
+                                 self.ws, self.ws_bytes)
+        return self.out_rec[:n], self.out_perm[:n]
+
+    def sort_text_whole(self, text, alg="auto", tune=None, max_words: int | None = None):
+        """Phase 1, then the unbucketed order; returns (out_rec, out_perm,
+        n_words device tensor, rec, len, src_off)."""
+        self._text_buffers(self.max_words if max_words is None else max_words)
         mw = self.max_words if max_words is None else max_words
+        bsort_sort_text_whole(text, text.numel(), self.W, mw, alg, tune, self.rec, self.len,
+                              self.src_off, self.n_words, self.out_rec, self.out_perm, self.ws,
+                              self.ws_bytes)
+        return self.out_rec, self.out_perm, self.n_words, self.rec, self.len, self.src_off
+
+    def pack(self, n: int, bucketed: bool = True, perm=None, ln=None, out_bytes=None):
+        """The sorted words in self.out_rec packed without padding (§3.1):
+        returns (bytes, offsets[n + 1]) as device tensors; lengths from the
+        bucket offsets (bucketed order) or from ln[perm] (any order)."""
+        torch = self.torch
+        cap = n * self.W
+        if out_bytes is None:
+            out_bytes = torch.empty(max(cap, 16), dtype=torch.uint8, device=self.device)
+        offsets = torch.empty(n + 1, dtype=torch.int32, device=self.device)
+        bsort_pack_words(n, self.W, self.out_rec, self.off if bucketed else None,
+                         None if bucketed else perm, None if bucketed else ln, out_bytes,
+                         int(out_bytes.numel()), offsets, self.ws, self.ws_bytes)
+        return out_bytes, offsets
+
+    def _text_buffers(self, mw: int):
+        torch = self.torch
         if self.rec is None or self.rec.shape[0] < max(mw, 1):
             self.rec = torch.empty((max(mw, 1), self.W), dtype=torch.uint8, device=self.device)
             self.len = torch.empty(max(mw, 1), dtype=torch.uint8, device=self.device)
             self.src_off = torch.empty(max(mw, 1), dtype=torch.int32, device=self.device)
             self.n_words = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def sort_text(self, text, alg="auto", tune=None, max_words: int | None = None):
+        """Phases 1-3 on raw text; returns (out_rec, out_perm, off, n_words device tensor,
+        rec, len, src_off).  Outputs past n_words are unspecified."""
+        mw = self.max_words if max_words is None else max_words
+        self._text_buffers(mw)
         bsort_sort_text(text, text.numel(), self.W, mw, alg, tune, self.rec, self.len,
                         self.src_off, self.n_words, self.out_rec, self.out_perm, self.off,
                         self.ws, self.ws_bytes)

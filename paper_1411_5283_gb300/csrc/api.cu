@@ -157,10 +157,16 @@ bsort_status bsort_gather(uint32_t n, uint32_t W, const uint32_t* d_off, const v
   return cuda_status(launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s));
 }
 
-bsort_status bsort_sort_records(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
-                                uint32_t W, bsort_alg alg, const bsort_tune* tune,
-                                uint8_t* d_out_rec, uint32_t* d_out_perm, uint32_t* d_off,
-                                void* d_ws, size_t ws_bytes, cudaStream_t s) {
+}  // extern "C"
+
+namespace {
+
+// The one-call paths, with the bucket offsets at d_off; whole = true adds the
+// merge of the buckets into the unbucketed order.
+bsort_status sort_records_impl(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n, uint32_t W,
+                               bsort_alg alg, const bsort_tune* tune, uint8_t* d_out_rec,
+                               uint32_t* d_out_perm, uint32_t* d_off, void* d_ws, size_t ws_bytes,
+                               bool whole, cudaStream_t s) {
   if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
   if (n && (!d_rec || !d_len || !d_out_rec || !d_out_perm)) return BSORT_E_INVALID;
   if (n && (!aligned(d_rec, 16) || !aligned(d_out_rec, 16))) return BSORT_E_INVALID;
@@ -173,19 +179,20 @@ bsort_status bsort_sort_records(const uint8_t* d_rec, const uint8_t* d_len, uint
   cudaError_t e;
   if (alg == BSORT_AUTO && auto_applies(n, ws, W)) {
     e = launch_auto(d_rec, d_len, n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
-    return cuda_status(e);
+  } else {
+    e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
+    if (e == cudaSuccess) e = launch_sort(n, W, p, d_off, ws, s);
+    if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
   }
-  e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
-  if (e == cudaSuccess) e = launch_sort(n, W, p, d_off, ws, s);
-  if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
+  if (e == cudaSuccess && whole) e = launch_whole(n, W, d_off, ws, d_out_rec, d_out_perm, s);
   return cuda_status(e);
 }
 
-bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
-                             uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
-                             uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
-                             uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
-                             uint32_t* d_off, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+bsort_status sort_text_impl(const uint8_t* d_text, uint64_t n_bytes, uint32_t W, uint32_t max_words,
+                            bsort_alg alg, const bsort_tune* tune, uint8_t* d_rec, uint8_t* d_len,
+                            uint32_t* d_src_off, uint32_t* d_n_words, uint8_t* d_out_rec,
+                            uint32_t* d_out_perm, uint32_t* d_off, void* d_ws, size_t ws_bytes,
+                            bool whole, cudaStream_t s) {
   if (!valid_W(W) || n_bytes > 0xFFFF0000ull || (n_bytes && !d_text) || !d_off || !d_n_words)
     return BSORT_E_INVALID;
   if (max_words > 0xFFFFFFFEu) return BSORT_E_INVALID;
@@ -202,13 +209,76 @@ bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W
                                   d_len, d_src_off, d_n_words, ws, s);
   if (e == cudaSuccess && alg == BSORT_AUTO && auto_applies(max_words, ws, W)) {
     e = launch_auto(d_rec, d_len, max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
-    return cuda_status(e);
+  } else {
+    if (e == cudaSuccess) e = launch_bucket(d_rec, d_len, max_words, d_n_words, W, d_off, ws, s);
+    if (e == cudaSuccess) e = launch_sort(max_words, W, p, d_off, ws, s);
+    if (e == cudaSuccess)
+      e = launch_gather(max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
   }
-  if (e == cudaSuccess) e = launch_bucket(d_rec, d_len, max_words, d_n_words, W, d_off, ws, s);
-  if (e == cudaSuccess) e = launch_sort(max_words, W, p, d_off, ws, s);
-  if (e == cudaSuccess)
-    e = launch_gather(max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
+  if (e == cudaSuccess && whole) e = launch_whole(max_words, W, d_off, ws, d_out_rec, d_out_perm, s);
   return cuda_status(e);
+}
+
+// Bucket offsets of the unbucketed calls live in the workspace.
+uint32_t* internal_off(void* d_ws, size_t ws_bytes, uint32_t W) {
+  if (!valid_W(W) || !d_ws || !aligned(d_ws, 256)) return nullptr;
+  return ws_view(d_ws, ws_bytes, W).misc;
+}
+
+}  // namespace
+
+extern "C" {
+
+bsort_status bsort_sort_records(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                uint8_t* d_out_rec, uint32_t* d_out_perm, uint32_t* d_off,
+                                void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  return sort_records_impl(d_rec, d_len, n, W, alg, tune, d_out_rec, d_out_perm, d_off, d_ws,
+                           ws_bytes, false, s);
+}
+
+bsort_status bsort_sort_text(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                             uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                             uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                             uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                             uint32_t* d_off, void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  return sort_text_impl(d_text, n_bytes, W, max_words, alg, tune, d_rec, d_len, d_src_off,
+                        d_n_words, d_out_rec, d_out_perm, d_off, d_ws, ws_bytes, false, s);
+}
+
+bsort_status bsort_sort_records_whole(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                      uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                      uint8_t* d_out_rec, uint32_t* d_out_perm, void* d_ws,
+                                      size_t ws_bytes, cudaStream_t s) {
+  uint32_t* off = internal_off(d_ws, ws_bytes, W);
+  if (!off) return valid_W(W) ? BSORT_E_WORKSPACE : BSORT_E_INVALID;
+  return sort_records_impl(d_rec, d_len, n, W, alg, tune, d_out_rec, d_out_perm, off, d_ws,
+                           ws_bytes, true, s);
+}
+
+bsort_status bsort_sort_text_whole(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                                   uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                                   uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                                   uint32_t* d_n_words, uint8_t* d_out_rec, uint32_t* d_out_perm,
+                                   void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  uint32_t* off = internal_off(d_ws, ws_bytes, W);
+  if (!off) return valid_W(W) ? BSORT_E_WORKSPACE : BSORT_E_INVALID;
+  return sort_text_impl(d_text, n_bytes, W, max_words, alg, tune, d_rec, d_len, d_src_off,
+                        d_n_words, d_out_rec, d_out_perm, off, d_ws, ws_bytes, true, s);
+}
+
+bsort_status bsort_pack_words(uint32_t n, uint32_t W, const uint8_t* d_rec, const uint32_t* d_off,
+                              const uint32_t* d_perm, const uint8_t* d_len, uint8_t* d_bytes,
+                              uint64_t bytes_cap, uint32_t* d_offsets, void* d_ws,
+                              size_t ws_bytes, cudaStream_t s) {
+  if (!valid_W(W) || !d_offsets) return BSORT_E_INVALID;
+  if (n > pack_max_words() || static_cast<uint64_t>(n) * W > 0xFFFFFFFFull) return BSORT_E_CAPACITY;
+  if (n && (!d_rec || !aligned(d_rec, 16) || !d_bytes)) return BSORT_E_INVALID;
+  if (n && !d_off && (!d_perm || !d_len)) return BSORT_E_INVALID;
+  if (const bsort_status e = check_ws(d_ws, ws_bytes, W, 0)) return e;
+  const Ws ws = ws_view(d_ws, ws_bytes, W);
+  return cuda_status(launch_pack(n, W, d_rec, d_off, d_perm, d_len, d_bytes, bytes_cap, d_offsets,
+                                 ws, s));
 }
 
 size_t bsort_sort_many_workspace_size(uint64_t total_words, uint32_t n_lists, uint32_t W) {

@@ -160,6 +160,7 @@ struct Ws {
   WsHeader* hdr;
   uint32_t* table;
   uint8_t* autoa;     // sample-sort area (samples, splitters, segment tables)
+  uint32_t* misc;     // 64 KB of small per-call state (e.g. internal bucket offsets)
   uint64_t* keys[2];
   uint32_t* idx[2];
   uint64_t cap;
@@ -178,6 +179,7 @@ inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
   w.idx[0] = reinterpret_cast<uint32_t*>(b + l.idx_a);
   w.idx[1] = reinterpret_cast<uint32_t*>(b + l.idx_b);
   w.autoa = reinterpret_cast<uint8_t*>(b + l.autoa);
+  w.misc = reinterpret_cast<uint32_t*>(b + l.misc);
   w.cap = l.cap;
   w.K = l.K;
   w.wait_polls = first_wait_polls();

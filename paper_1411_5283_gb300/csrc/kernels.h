@@ -68,6 +68,22 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
 cudaError_t launch_gather(uint32_t n_cap, const uint32_t* d_n, uint32_t W, const uint32_t* d_off,
                           const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
 
+// Unbucketed order (whole.cu): merges the length buckets of a bucketed answer
+// in out_rec / out_perm (offsets d_off) into one run ordered by bytes, a
+// proper prefix first, then input index.  Uses the workspace's key and index
+// planes as scratch.
+cudaError_t launch_whole(uint32_t n_cap, uint32_t W, const uint32_t* d_off, const Ws& ws,
+                         uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
+
+// Packed output (pack.cu): the sorted records rec[n][W] back to back without
+// padding, offsets[n + 1].  Lengths from the bucket offsets d_off (bucketed
+// order) or, when d_off is null, len[perm[r]].  Needs n_cap <= pack_max_words()
+// and n_cap W < 2^32; a total above cap records BSORT_E_CAPACITY.
+uint32_t pack_max_words();
+cudaError_t launch_pack(uint32_t n_cap, uint32_t W, const uint8_t* rec, const uint32_t* d_off,
+                        const uint32_t* perm, const uint8_t* len, uint8_t* bytes, uint64_t cap,
+                        uint32_t* offsets, const Ws& ws, cudaStream_t s);
+
 // Batched sort (sort_many.cu).
 size_t many_workspace_size(uint64_t total_words, uint32_t n_lists, uint32_t W);
 uint64_t many_capacity(size_t ws_bytes, uint32_t W, uint32_t n_lists);

@@ -13,7 +13,10 @@ def need_cuda():
 
 
 def to_dev(a: np.ndarray, torch, dtype=None):
-    t = torch.from_numpy(np.ascontiguousarray(a))
+    a = np.ascontiguousarray(a)
+    if not a.flags.writeable:
+        a = a.copy()
+    t = torch.from_numpy(a)
     if dtype is not None:
         t = t.view(dtype)
     return t.cuda()
