@@ -73,9 +73,17 @@ typedef enum { BSORT_ODD_EVEN = 0, BSORT_MERGE = 1, BSORT_AUTO = 2 } bsort_alg;
  *  tile               elements per bitonic tile (power of two, 256..4096)
  *  oddeven_max        elements per odd-even tile (power of two, 64..2048)
  *  threads_per_bucket threads per tile-sort CTA (128, 256, 512 or 1024)
- *  merge_fanin        elements per merge-path partition (power of two, 512..4096) */
+ *  merge_fanin        elements per merge-path partition (power of two, 512..4096)
+ *  oddeven_cross      BSORT_MERGE (and AUTO where it takes the merge path):
+ *                     the crossover between the paper's two sorts.  A length
+ *                     bucket of at most this many words (1..tile) is sorted
+ *                     whole by odd-even transposition in one shared-memory
+ *                     tile (bubble sort's data-parallel form, §2); a larger
+ *                     one by bitonic tiles and merge-path merges (§4-§5).
+ *                     1 = never odd-even (a one-word bucket is sorted);
+ *                     0 = the library default (64). */
 typedef struct {
-  uint32_t tile, oddeven_max, threads_per_bucket, merge_fanin;
+  uint32_t tile, oddeven_max, threads_per_bucket, merge_fanin, oddeven_cross;
 } bsort_tune;
 
 /* One list of a batched call (bsort_sort_many).

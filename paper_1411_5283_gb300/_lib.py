@@ -32,7 +32,8 @@ class BsortError(RuntimeError):
 
 class Tune(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_uint32), ("oddeven_max", ctypes.c_uint32),
-                ("threads_per_bucket", ctypes.c_uint32), ("merge_fanin", ctypes.c_uint32)]
+                ("threads_per_bucket", ctypes.c_uint32), ("merge_fanin", ctypes.c_uint32),
+                ("oddeven_cross", ctypes.c_uint32)]
 
 
 class ListDesc(ctypes.Structure):

@@ -3,7 +3,8 @@
 For a device, record width W, algorithm and size class (n rounded up to a
 power of two) it times every candidate setting of tile size (bitonic),
 odd-even tile size, threads per tile-sort CTA and merge-path partition size,
-keeps the fastest, and caches it as JSON keyed by device name, SM count, W,
+then, for the merge path, the bucket-size crossover below which a bucket is
+sorted whole by odd-even transposition; it keeps the fastest, and caches it as JSON keyed by device name, SM count, W,
 algorithm, size class and call kind (single list or batched).  Results never
 depend on the knobs; only the time does.
 """
@@ -48,6 +49,17 @@ def candidates(alg: str, W: int) -> list[dict]:
     return out
 
 
+# odd-even / merge crossovers swept for the MERGE path (words per bucket sorted
+# whole by odd-even transposition; 1 = never)
+CROSSOVERS = (1, 16, 32, 64, 128, 256, 512, 1024)
+
+
+def crossover_candidates(base: dict) -> list[dict]:
+    """The base setting with every crossover that fits its tile."""
+    tile = base.get("tile", 2048)
+    return [dict(base, oddeven_cross=x) for x in CROSSOVERS if x <= tile]
+
+
 def load_cache(path: str | None = None) -> dict:
     path = path or cache_path()
     try:
@@ -82,14 +94,23 @@ def lookup(key: str, path: str | None = None) -> dict | None:
 
 
 def tune(key: str, time_fn: Callable[[dict], float], cands: list[dict],
-         path: str | None = None, force: bool = False) -> dict:
+         path: str | None = None, force: bool = False,
+         refine: Callable[[dict], list[dict]] | None = None) -> dict:
     """Returns the cached setting for key, or sweeps cands with time_fn and
-    caches the fastest."""
+    caches the fastest.  refine(best) may list a second sweep around the
+    first one's winner (the merge path's odd-even crossover)."""
     cache = load_cache(path)
     if not force and key in cache:
         return dict(cache[key]["tune"])
     best, t = choose(time_fn, cands)
-    cache[key] = {"tune": best, "seconds": t, "candidates": len(cands)}
+    n = len(cands)
+    if refine is not None:
+        # the second sweep includes the winner's own setting (the default
+        # crossover is one of its values), so its fastest entry is kept
+        more = refine(best)
+        best, t = choose(time_fn, more)
+        n += len(more)
+    cache[key] = {"tune": best, "seconds": t, "candidates": n}
     save_cache(cache, path)
     return dict(best)
 
@@ -129,7 +150,7 @@ def tune_records(sorter, rec, ln, n: int, alg: str = "merge", path: str | None =
     cands = candidates(alg, sorter.W)[:max_candidates]
     key = tune_key(name, sms, sorter.W, alg, n, "single")
     return tune(key, lambda c: cuda_timer(lambda: sorter.sort_records(rec, ln, n, alg=alg, tune=c)),
-                cands, path, force)
+                cands, path, force, crossover_candidates if alg != "odd_even" else None)
 
 
 def tune_batch(bsorter, data, ln, *, text: bool, max_list_words: int, total_words: int,
@@ -140,4 +161,5 @@ def tune_batch(bsorter, data, ln, *, text: bool, max_list_words: int, total_word
     cands = candidates(alg, bsorter.W)[:max_candidates]
     key = tune_key(name, sms, bsorter.W, alg, total_words, "batched")
     return tune(key, lambda c: cuda_timer(lambda: bsorter.run(
-        data, ln, text=text, max_list_words=max_list_words, alg=alg, tune=c)), cands, path, force)
+        data, ln, text=text, max_list_words=max_list_words, alg=alg, tune=c)), cands, path, force,
+        crossover_candidates if alg != "odd_even" else None)

@@ -34,8 +34,9 @@ bsort_status check_ws(const void* d_ws, size_t ws_bytes, uint32_t W, uint64_t ne
   return BSORT_OK;
 }
 
-// Resolves the algorithm and tuning knobs; returns false on an invalid knob.
-bool resolve(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
+}  // namespace
+
+bool bsort::resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
   bsort_tune t{};
   if (tune) t = *tune;
   const uint32_t KW = W / 8;
@@ -53,7 +54,19 @@ bool resolve(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
   if (!pow2(p->part) || p->part < 256 || p->part > 4096) return false;
   if (2ull * p->part * (8 * KW + 4) > 200 * 1024) return false;  // merge CTA shared memory
   if (p->part > 2 * p->tile) p->part = 2 * p->tile;  // a partition never spans two run pairs
+  if (p->alg == BSORT_ODD_EVEN) {
+    p->cross = 0xFFFFFFFFu;  // every tile by odd-even transposition
+  } else {
+    p->cross = t.oddeven_cross ? t.oddeven_cross : kDefaultCross;
+    if (p->cross > p->tile) return false;
+  }
   return true;
+}
+
+namespace {
+
+bool resolve(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
+  return resolve_params(alg, tune, W, p);
 }
 
 }  // namespace

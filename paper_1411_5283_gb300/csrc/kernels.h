@@ -57,7 +57,15 @@ struct SortParams {
   uint32_t tile;       // elements per tile
   uint32_t threads;    // threads per tile-sort CTA
   uint32_t part;       // elements per merge-path partition
+  uint32_t cross;      // buckets of at most this many words take the odd-even tile
 };
+
+// Default odd-even / merge crossover of the MERGE path (words per bucket).
+constexpr uint32_t kDefaultCross = 64;
+
+// Resolves the algorithm and tuning knobs of a call on records of width W
+// (tune may be null); returns false on an invalid knob.
+bool resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p);
 
 // Phase 3: tile sort of every bucket, then merge passes until each bucket is
 // one run.  n_cap bounds the word count (sizes the grids).

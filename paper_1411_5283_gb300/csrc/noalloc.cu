@@ -113,21 +113,8 @@ extern "C" bsort_status bsort_sort_records_noalloc(const uint8_t* d_rec, const u
   if (n && ((reinterpret_cast<uintptr_t>(d_rec) | reinterpret_cast<uintptr_t>(d_out_rec)) & 15u))
     return BSORT_E_INVALID;
   // Same knobs and defaults as bsort_sort_records.
-  bsort_tune t{};
-  if (tune) t = *tune;
   SortParams p;
-  p.alg = alg == BSORT_ODD_EVEN ? BSORT_ODD_EVEN : BSORT_MERGE;
-  p.tile = p.alg == BSORT_ODD_EVEN ? (t.oddeven_max ? t.oddeven_max : 512u) : (t.tile ? t.tile : 2048u);
-  p.threads = t.threads_per_bucket ? t.threads_per_bucket : 256u;
-  p.part = t.merge_fanin ? t.merge_fanin : (W / 8 >= 3 ? 1024u : 2048u);
-  const auto pow2 = [](uint32_t x) { return x && !(x & (x - 1)); };
-  if (!pow2(p.tile) || p.tile < 64 || p.tile > 4096 || (p.alg == BSORT_MERGE && p.tile < 256) ||
-      (p.alg == BSORT_ODD_EVEN && p.tile > 2048))
-    return BSORT_E_INVALID;
-  if (p.threads < 64 || p.threads > 1024 || p.threads % 32) return BSORT_E_INVALID;
-  if (!pow2(p.part) || p.part < 256 || p.part > 4096) return BSORT_E_INVALID;
-  if (2ull * p.part * (8 * (W / 8) + 4) > 200 * 1024) return BSORT_E_INVALID;
-  if (p.part > 2 * p.tile) p.part = 2 * p.tile;
+  if (!resolve_params(alg, tune, W, &p)) return BSORT_E_INVALID;
 
   void* ws_ptr = nullptr;
   if (noalloc_ptr(&ws_ptr) != cudaSuccess) return BSORT_E_CUDA;

@@ -44,8 +44,11 @@ __device__ TileRef find_tile(const uint32_t* s_off, uint32_t W, uint32_t T, uint
   return r;
 }
 
+// A bucket of at most `cross` words is sorted whole by odd-even
+// transposition (it fits one tile); a larger one by bitonic tiles, merged
+// afterwards.  cross = 0xFFFFFFFF makes every tile odd-even.
 __global__ void tile_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t T,
-                                 uint32_t part, int odd_even, Ws ws) {
+                                 uint32_t cross, Ws ws) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2];
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
@@ -60,6 +63,7 @@ __global__ void tile_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W,
   const TileRef tr = find_tile(s_off, W, T, blockIdx.x);
   if (!tr.valid) return;
   uint8_t* sm = align128(smem);
+  const bool odd_even = s_off[tr.L + 1] - s_off[tr.L] <= cross;
   switch (keys_for_len(tr.L)) {
     case 1: sort_one_tile<1>(sm, T, tr, odd_even, ws); break;
     case 2: sort_one_tile<2>(sm, T, tr, odd_even, ws); break;
@@ -113,7 +117,7 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   if (e != cudaSuccess) return e;
   const uint32_t tiles = (n_cap + T - 1) / T + W;
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "tile_odd_even" : "tile_bitonic", tile_sort_kernel, tiles,
-               p.threads, tsm, s, d_off, W, T, p.part, p.alg == BSORT_ODD_EVEN ? 1 : 0, ws);
+               p.threads, tsm, s, d_off, W, T, p.cross, ws);
   const uint32_t parts = (n_cap + part - 1) / part + W;
   int src = 0;
   for (uint64_t R = T; R < n_cap; R <<= 1) {

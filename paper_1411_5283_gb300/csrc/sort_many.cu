@@ -429,7 +429,9 @@ __global__ void __launch_bounds__(1024) many_tplan_kernel(Many m) {
   if (threadIdx.x == 0) m.hdr->tiles = tot;
 }
 
-__global__ void many_tile_kernel(Many m, int odd_even) {
+// A (list, length) bucket of at most `cross` words is sorted whole by
+// odd-even transposition; a larger one by bitonic tiles (merged afterwards).
+__global__ void many_tile_kernel(Many m, uint32_t cross) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sm = align128(smem);
   const uint32_t S = m.n_lists * m.W, T = m.T;
@@ -441,11 +443,12 @@ __global__ void many_tile_kernel(Many m, int odd_even) {
     tr.start = m.seg_start[s] + (t - m.tile_pre[s]) * T;
     tr.len = min(T, m.seg_start[s] + m.seg_cnt[s] - tr.start);
     tr.valid = true;
+    const bool odd_even = m.seg_cnt[s] <= cross;
     switch (keys_for_len(tr.L)) {
-      case 1: sort_one_tile<1>(sm, T, tr, odd_even != 0, m.ws); break;
-      case 2: sort_one_tile<2>(sm, T, tr, odd_even != 0, m.ws); break;
-      case 3: sort_one_tile<3>(sm, T, tr, odd_even != 0, m.ws); break;
-      default: sort_one_tile<4>(sm, T, tr, odd_even != 0, m.ws); break;
+      case 1: sort_one_tile<1>(sm, T, tr, odd_even, m.ws); break;
+      case 2: sort_one_tile<2>(sm, T, tr, odd_even, m.ws); break;
+      case 3: sort_one_tile<3>(sm, T, tr, odd_even, m.ws); break;
+      default: sort_one_tile<4>(sm, T, tr, odd_even, m.ws); break;
     }
     __syncthreads();
   }
@@ -568,7 +571,7 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   BSORT_LAUNCH("many_scatter", many_scatter_kernel, grid, kThreads, 0, s, text_or_rec, len, text, m);
   BSORT_LAUNCH("many_tplan", many_tplan_kernel, 1, 1024, 0, s, m);
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "many_tile_odd_even" : "many_tile_bitonic", many_tile_kernel,
-               grid, p.threads, tsm, s, m, p.alg == BSORT_ODD_EVEN ? 1 : 0);
+               grid, p.threads, tsm, s, m, p.cross);
   int src = 0;
   for (uint64_t R = p.tile; R < max_list_words; R <<= 1) {
     BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m, static_cast<uint32_t>(R));

@@ -47,6 +47,24 @@ def test_cache_roundtrip_and_reuse(tmp_path):
     assert at.lookup(key, path) == {"tile": 1024}
 
 
+def test_refine_sweeps_crossovers_of_the_winner(tmp_path):
+    path = str(tmp_path / "tune.json")
+    cs = [{"tile": 1024}, {"tile": 2048}]
+    seen = []
+
+    def fake(c):
+        seen.append(dict(c))
+        if "oddeven_cross" in c:
+            return 0.5 + abs(c["oddeven_cross"] - 128) / 1e4  # 128 is fastest
+        return 1.0 if c["tile"] == 2048 else 2.0
+
+    best = at.tune("k", fake, cs, path, refine=at.crossover_candidates)
+    assert best == {"tile": 2048, "oddeven_cross": 128}
+    assert {c.get("oddeven_cross") for c in seen[2:]} == set(at.CROSSOVERS)
+    assert at.load_cache(path)["k"]["tune"]["oddeven_cross"] == 128
+    assert all(c["oddeven_cross"] <= 256 for c in at.crossover_candidates({"tile": 256}))
+
+
 def test_size_class():
     assert at.size_class(1) == 1 and at.size_class(1000) == 1024 and at.size_class(1024) == 1024
 
@@ -59,8 +77,10 @@ def test_tuned_knobs_keep_the_answer(orc, tmp_path):
     rec, ln = table(5, 50_000, 16, b"abcdefgh", 7)
     s = bs.Sorter(ln.size, 16)
     d_rec, d_len = to_dev(rec, torch), to_dev(ln, torch)
-    best = at.tune_records(s, d_rec, d_len, ln.size, "merge", path=str(tmp_path / "t.json"),
-                           max_candidates=6)
+    path = str(tmp_path / "t.json")
+    best = at.tune_records(s, d_rec, d_len, ln.size, "merge", path=path, max_candidates=6)
+    assert "oddeven_cross" in best  # the crossover sweep ran and its winner is cached
+    assert at.load_cache(path)[next(iter(at.load_cache(path)))]["tune"] == best
     out = s.sort_records(d_rec, d_len, ln.size, alg="merge", tune=best)
     torch.cuda.synchronize()
     assert_same_answer(*out, orc.stable_sort(orc.Words(rec, ln)), ln.size)

@@ -150,3 +150,22 @@ def test_graph_replay_equals_direct(env):
     for i in (0, 17, 63):
         r, l = rec[starts[i]:starts[i + 1]], ln[starts[i]:starts[i + 1]]
         check_list(b, desc, i, r, l, orc)
+
+
+@pytest.mark.parametrize("cross", [1, 128, 2048])
+def test_crossover_keeps_every_list(env, cross):
+    """(list, length) buckets of at most cross words take the odd-even tile,
+    larger ones bitonic tiles and merges; every list stays the oracle's."""
+    torch, bs, batch, orc = env
+    W = 16
+    sizes = [70, 900, 2100, 30_000, 5]
+    lists = [synth.list_words(800 + i, m, 50_000, W) for i, m in enumerate(sizes)]
+    rec, ln = concat(lists, W)
+    desc = batch.record_lists(sizes)
+    b = batch.BatchSorter(ln.size, len(sizes), W)
+    b.set_lists(desc)
+    b.run(to_dev(rec, torch), to_dev(ln, torch), text=False, max_list_words=max(sizes),
+          alg="merge", tune=dict(tile=2048, oddeven_cross=cross))
+    torch.cuda.synchronize()
+    for i, (r, l) in enumerate(lists):
+        check_list(b, desc, i, r, l, orc)

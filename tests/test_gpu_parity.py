@@ -233,3 +233,20 @@ def test_errors_reported(env):
     s = bs.Sorter(16, 32)
     s.sort_text(to_dev(np.frombuffer(text, np.uint8), torch))
     assert s.status() == 2
+
+
+@pytest.mark.parametrize("cross", [1, 2, 64, 700, 2048])
+def test_odd_even_merge_crossover_keeps_the_answer(env, cross):
+    """Buckets from a handful of words (lengths near 32) to tens of thousands
+    (length 3): with the crossover at cross, buckets of at most cross words
+    are sorted whole by odd-even transposition, the rest by bitonic tiles and
+    merges; the answer is the oracle's for every crossover."""
+    torch, bs, orc = env
+    rec, ln = synth.large_records(13, 60_000, 32)
+    counts = np.bincount(ln, minlength=33)[1:]
+    assert counts.min() <= 64 and counts.max() > 2048  # buckets on both sides
+    expect = orc.stable_sort(orc.Words(rec, ln))
+    s, out_rec, out_perm, off = run_records(env, rec, ln, "merge",
+                                            tune=dict(tile=2048, oddeven_cross=cross))
+    assert s.status() == 0
+    assert_same_answer(out_rec, out_perm, off, expect, ln.size)
