@@ -72,7 +72,10 @@ typedef enum { BSORT_ODD_EVEN = 0, BSORT_MERGE = 1, BSORT_AUTO = 2 } bsort_alg;
  * depend on them.
  *  tile               elements per bitonic tile (power of two, 256..4096)
  *  oddeven_max        elements per odd-even tile (power of two, 64..2048)
- *  threads_per_bucket threads per tile-sort CTA (128, 256, 512 or 1024)
+ *  threads_per_bucket threads per tile-sort CTA (a multiple of 32, 64..1024;
+ *                     default 256 for odd-even tiles, tile / 4 for bitonic
+ *                     tiles, which then hold 2, 4 or (one key word) 8
+ *                     positions per thread in registers)
  *  merge_fanin        elements per merge-path partition (power of two, 512..4096)
  *  oddeven_cross      BSORT_MERGE (and AUTO where it takes the merge path):
  *                     the crossover between the paper's two sorts.  A length

@@ -48,7 +48,9 @@ bool bsort::resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, So
     p->tile = t.tile ? t.tile : 2048;
     if (!pow2(p->tile) || p->tile < 256 || p->tile > 4096) return false;
   }
-  p->threads = t.threads_per_bucket ? t.threads_per_bucket : 256;
+  // bitonic tiles sort four positions per thread in registers by default
+  p->threads = t.threads_per_bucket ? t.threads_per_bucket
+                                    : (p->alg == BSORT_ODD_EVEN ? 256u : (p->tile / 4 < 64 ? 64u : p->tile / 4));
   if (p->threads < 64 || p->threads > 1024 || p->threads % 32) return false;
   p->part = t.merge_fanin ? t.merge_fanin : (KW >= 3 ? 1024u : 2048u);
   if (!pow2(p->part) || p->part < 256 || p->part > 4096) return false;

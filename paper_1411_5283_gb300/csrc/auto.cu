@@ -311,144 +311,6 @@ auto_sample_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ 
   v.samp32[p.s32 + slot] = i;
 }
 
-// ---- register bitonic network (the splitters' sample chunks) -------------
-// Sorts N = E * blockDim.x positions held in registers, blocked layout:
-// thread t holds positions t*E .. t*E+E-1 in r[].  All-ascending form: for
-// each block size k the first step pairs i with i ^ (k-1), the next ones pair
-// i with i ^ j (j = k/4 .. 1); the lower position keeps the smaller value.
-// A partner in the same thread is compared in registers, one in the same warp
-// through __shfl_xor_sync, one in another warp through shared memory, so only
-// those steps need block barriers.
-
-// Padded exchange position: one spare slot per 16 keeps the strided exchange
-// accesses free of bank conflicts.
-__host__ __device__ constexpr uint32_t pad16(uint32_t i) { return i + (i >> 4); }
-
-template <int K>
-__device__ __forceinline__ Elem<K> elem_inf() {
-  Elem<K> e;
-#pragma unroll
-  for (int k = 0; k < K; ++k) e.k[k] = ~0ull;
-  e.idx = ~0u;
-  return e;
-}
-
-// (key words, index) elements; exchange slots in the tile's planes.
-template <int K>
-struct ElemOps {
-  using T = Elem<K>;
-  SmemTile<K> t;
-  __device__ static bool less(const Elem<K>& a, const Elem<K>& b) { return elem_less<K>(a, b); }
-  __device__ static Elem<K> shfl(const Elem<K>& x, uint32_t m) {
-    Elem<K> y;
-#pragma unroll
-    for (int k = 0; k < K; ++k) y.k[k] = __shfl_xor_sync(0xffffffffu, x.k[k], m);
-    y.idx = __shfl_xor_sync(0xffffffffu, x.idx, m);
-    return y;
-  }
-  __device__ static Elem<K> inf() { return elem_inf<K>(); }
-  __device__ void st(uint32_t i, const Elem<K>& v) const { t.put(pad16(i), v); }
-  __device__ Elem<K> ld(uint32_t i) const { return t.get(pad16(i)); }
-};
-
-template <typename Ops, int M, int E>
-__device__ __forceinline__ void reg_step(typename Ops::T (&r)[E]) {
-  if constexpr (M < E) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      constexpr int m = M;
-      const int q = j ^ m;
-      if (q > j && Ops::less(r[q], r[j])) {
-        const typename Ops::T x = r[j];
-        r[j] = r[q];
-        r[q] = x;
-      }
-    }
-  }
-}
-
-template <typename Ops, int E>
-__device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops& ops, uint32_t mask) {
-  using T = typename Ops::T;
-  constexpr uint32_t LE = E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4;
-  const uint32_t tid = threadIdx.x;
-  const uint32_t lane_mask = mask >> LE;
-  if (mask < E) {
-    // in registers: masks are the flips 1, 3, 7, 15 or the cleaners 1, 2, 4, 8
-    switch (mask) {
-      case 1: reg_step<Ops, 1, E>(r); break;
-      case 2: reg_step<Ops, 2, E>(r); break;
-      case 3: reg_step<Ops, 3, E>(r); break;
-      case 4: reg_step<Ops, 4, E>(r); break;
-      case 7: reg_step<Ops, 7, E>(r); break;
-      case 8: reg_step<Ops, 8, E>(r); break;
-      default: reg_step<Ops, 15, E>(r); break;
-    }
-  } else if (lane_mask < 32) {
-    // across lanes of one warp; my position is the upper one of its pair when
-    // the highest bit of the lane part of the mask is set in my lane
-    const uint32_t top = 1u << (31 - __clz(lane_mask));
-    const bool keep_small = (tid & top) == 0;
-    if ((mask & (E - 1)) == 0) {
-      // cleaner step: the partner holds the same slot j
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const T other = Ops::shfl(r[j], lane_mask);
-        if (Ops::less(other, r[j]) == keep_small) r[j] = other;
-      }
-    } else {
-      // flip step (mask = k - 1): slot j pairs with the partner's slot E-1-j.
-      // Slots j and E-1-j are exchanged together: sending slot E-1-j delivers
-      // the partner's value for my slot j, sending slot j the one for E-1-j.
-#pragma unroll
-      for (int j = 0; j < E / 2; ++j) {
-        const T for_j = Ops::shfl(r[E - 1 - j], lane_mask);
-        const T for_m = Ops::shfl(r[j], lane_mask);
-        if (Ops::less(for_j, r[j]) == keep_small) r[j] = for_j;
-        if (Ops::less(for_m, r[E - 1 - j]) == keep_small) r[E - 1 - j] = for_m;
-      }
-    }
-  } else {
-    // across warps: exchange through shared memory
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < E; ++j) ops.st(tid * E + j, r[j]);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const uint32_t i = tid * E + j, pi = i ^ mask;
-      const T other = ops.ld(pi);
-      if (Ops::less(other, r[j]) == (i < pi)) r[j] = other;
-    }
-  }
-}
-
-// Sorts the first c values (read by get(i), unpadded) with a register bitonic
-// network of E per thread and hands them to sink(pos, value).  Needs
-// c <= E * blockDim.x; ops' exchange slots must hold pad16(E*blockDim.x - 1) + 1.
-template <typename Ops, int E, typename Get, typename Sink>
-__device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
-  using T = typename Ops::T;
-  const uint32_t tid = threadIdx.x;
-  T r[E];
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const uint32_t i = tid * E + j;
-    r[j] = i < c ? get(i) : Ops::inf();
-  }
-  uint32_t N = 2;
-  while (N < c) N <<= 1;
-  if (N < E) N = E;
-  for (uint32_t k = 2; k <= N; k <<= 1) {
-    bitonic_step<Ops, E>(r, ops, k - 1);
-    for (uint32_t j = k >> 2; j > 0; j >>= 1) bitonic_step<Ops, E>(r, ops, j);
-  }
-#pragma unroll
-  for (int j = 0; j < E; ++j)
-    if (tid * E + j < c) sink(tid * E + j, r[j]);
-  __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 // 2. splitters and region layout
 // ---------------------------------------------------------------------------

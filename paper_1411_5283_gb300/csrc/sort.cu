@@ -47,7 +47,7 @@ __device__ TileRef find_tile(const uint32_t* s_off, uint32_t W, uint32_t T, uint
 // A bucket of at most `cross` words is sorted whole by odd-even
 // transposition (it fits one tile); a larger one by bitonic tiles, merged
 // afterwards.  cross = 0xFFFFFFFF makes every tile odd-even.
-__global__ void tile_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t T,
+__global__ void __launch_bounds__(1024) tile_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t T,
                                  uint32_t cross, Ws ws) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2];

@@ -116,10 +116,157 @@ __device__ void odd_even_tile(const SmemTile<K>& t, uint32_t len) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register bitonic network (tile sorts of the merge path, the sample sort's
+// splitter chunks)
+// ---------------------------------------------------------------------------
+// Sorts N = E * blockDim.x positions held in registers, blocked layout:
+// thread t holds positions t*E .. t*E+E-1 in r[].  All-ascending form: for
+// each block size k the first step pairs i with i ^ (k-1), the next ones pair
+// i with i ^ j (j = k/4 .. 1); the lower position keeps the smaller value.
+// A partner in the same thread is compared in registers, one in the same warp
+// through __shfl_xor_sync, one in another warp through shared memory, so only
+// those steps need block barriers.
+
+// Padded exchange position: one spare slot per 16 keeps the strided exchange
+// accesses free of bank conflicts.
+__host__ __device__ constexpr uint32_t pad16(uint32_t i) { return i + (i >> 4); }
+
+template <int K>
+__device__ __forceinline__ Elem<K> elem_inf() {
+  Elem<K> e;
+#pragma unroll
+  for (int k = 0; k < K; ++k) e.k[k] = ~0ull;
+  e.idx = ~0u;
+  return e;
+}
+
+// (key words, index) elements; exchange slots in the tile's planes.
+template <int K>
+struct ElemOps {
+  using T = Elem<K>;
+  SmemTile<K> t;
+  __device__ static bool less(const Elem<K>& a, const Elem<K>& b) { return elem_less<K>(a, b); }
+  __device__ static Elem<K> shfl(const Elem<K>& x, uint32_t m) {
+    Elem<K> y;
+#pragma unroll
+    for (int k = 0; k < K; ++k) y.k[k] = __shfl_xor_sync(0xffffffffu, x.k[k], m);
+    y.idx = __shfl_xor_sync(0xffffffffu, x.idx, m);
+    return y;
+  }
+  __device__ static Elem<K> inf() { return elem_inf<K>(); }
+  __device__ void st(uint32_t i, const Elem<K>& v) const { t.put(pad16(i), v); }
+  __device__ Elem<K> ld(uint32_t i) const { return t.get(pad16(i)); }
+};
+
+template <typename Ops, int M, int E>
+__device__ __forceinline__ void reg_step(typename Ops::T (&r)[E]) {
+  if constexpr (M < E) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      constexpr int m = M;
+      const int q = j ^ m;
+      if (q > j && Ops::less(r[q], r[j])) {
+        const typename Ops::T x = r[j];
+        r[j] = r[q];
+        r[q] = x;
+      }
+    }
+  }
+}
+
+template <typename Ops, int E>
+__device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops& ops, uint32_t mask) {
+  using T = typename Ops::T;
+  constexpr uint32_t LE = E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane_mask = mask >> LE;
+  if (mask < E) {
+    // in registers: masks are the flips 1, 3, 7, 15 or the cleaners 1, 2, 4, 8
+    switch (mask) {
+      case 1: reg_step<Ops, 1, E>(r); break;
+      case 2: reg_step<Ops, 2, E>(r); break;
+      case 3: reg_step<Ops, 3, E>(r); break;
+      case 4: reg_step<Ops, 4, E>(r); break;
+      case 7: reg_step<Ops, 7, E>(r); break;
+      case 8: reg_step<Ops, 8, E>(r); break;
+      default: reg_step<Ops, 15, E>(r); break;
+    }
+  } else if (lane_mask < 32) {
+    // across lanes of one warp; my position is the upper one of its pair when
+    // the highest bit of the lane part of the mask is set in my lane
+    const uint32_t top = 1u << (31 - __clz(lane_mask));
+    const bool keep_small = (tid & top) == 0;
+    if ((mask & (E - 1)) == 0) {
+      // cleaner step: the partner holds the same slot j
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const T other = Ops::shfl(r[j], lane_mask);
+        if (Ops::less(other, r[j]) == keep_small) r[j] = other;
+      }
+    } else {
+      // flip step (mask = k - 1): slot j pairs with the partner's slot E-1-j.
+      // Slots j and E-1-j are exchanged together: sending slot E-1-j delivers
+      // the partner's value for my slot j, sending slot j the one for E-1-j.
+#pragma unroll
+      for (int j = 0; j < E / 2; ++j) {
+        const T for_j = Ops::shfl(r[E - 1 - j], lane_mask);
+        const T for_m = Ops::shfl(r[j], lane_mask);
+        if (Ops::less(for_j, r[j]) == keep_small) r[j] = for_j;
+        if (Ops::less(for_m, r[E - 1 - j]) == keep_small) r[E - 1 - j] = for_m;
+      }
+    }
+  } else {
+    // across warps: exchange through shared memory
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) ops.st(tid * E + j, r[j]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const uint32_t i = tid * E + j, pi = i ^ mask;
+      const T other = ops.ld(pi);
+      if (Ops::less(other, r[j]) == (i < pi)) r[j] = other;
+    }
+  }
+}
+
+// Sorts the first c values (read by get(i), unpadded) with a register bitonic
+// network of E per thread and hands them to sink(pos, value).  Needs
+// c <= E * blockDim.x; ops' exchange slots must hold pad16(E*blockDim.x - 1) + 1.
+template <typename Ops, int E, typename Get, typename Sink>
+__device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
+  using T = typename Ops::T;
+  const uint32_t tid = threadIdx.x;
+  T r[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const uint32_t i = tid * E + j;
+    r[j] = i < c ? get(i) : Ops::inf();
+  }
+  uint32_t N = 2;
+  while (N < c) N <<= 1;
+  if (N < E) N = E;
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    bitonic_step<Ops, E>(r, ops, k - 1);
+    for (uint32_t j = k >> 2; j > 0; j >>= 1) bitonic_step<Ops, E>(r, ops, j);
+  }
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (tid * E + j < c) sink(tid * E + j, r[j]);
+  __syncthreads();
+}
+
+// Exchange slots of the register network over T positions (padded by pad16).
+__host__ __device__ constexpr uint32_t tile_xslots(uint32_t T) { return T + T / 16; }
+
 // Shared memory of a tile-sort CTA: [mbarrier 16 B][KW key planes of T+2][idx T+4],
-// plus 128 bytes of slack to align the start.
+// then the register network's exchange planes (KW key planes and an index
+// plane of tile_xslots(T) slots), plus 128 bytes of slack to align the start.
 __host__ __device__ inline size_t tile_smem_bytes(uint32_t KW, uint32_t T) {
-  return 128 + 16 + static_cast<size_t>(KW) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
+  const size_t planes = static_cast<size_t>(KW) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
+  const size_t xch = static_cast<size_t>(tile_xslots(T)) * (8 * KW + 4);
+  return 128 + 16 + ((planes + 15) & ~size_t(15)) + xch;
 }
 
 __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
@@ -166,10 +313,31 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
 #pragma unroll
   for (int j = 0; j < K; ++j) t.k[j] = kplane + j * (T + 2) + (tr.start - ks);
   t.idx = iplane + (tr.start - is);
-  if (odd_even)
+  const uint32_t E = T / blockDim.x;
+  if (odd_even) {
     odd_even_tile<K>(t, tr.len);
-  else
+  } else if (T % blockDim.x == 0 && (E == 2 || (E == 4 && K <= 2) || (E == 8 && K == 1))) {
+    // bitonic network over registers, E positions per thread; only the
+    // cross-warp steps go through shared memory (one barrier pair each)
+    const size_t planes = static_cast<size_t>(K) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
+    uint8_t* xb = smem + 16 + ((planes + 15) & ~size_t(15));
+    const uint32_t X = tile_xslots(T);
+    SmemTile<K> xt;
+#pragma unroll
+    for (int j = 0; j < K; ++j) xt.k[j] = reinterpret_cast<uint64_t*>(xb) + j * X;
+    xt.idx = reinterpret_cast<uint32_t*>(xb + static_cast<size_t>(K) * X * 8);
+    const ElemOps<K> ops{xt};
+    auto get = [&](uint32_t i) { return t.get(i); };
+    auto sink = [&](uint32_t i, const Elem<K>& e) { t.put(i, e); };
+    if (E == 2) {
+      block_sort<ElemOps<K>, 2>(ops, tr.len, get, sink);
+    } else if constexpr (K <= 2) {
+      if (E == 4) block_sort<ElemOps<K>, 4>(ops, tr.len, get, sink);
+      else if constexpr (K == 1) block_sort<ElemOps<K>, 8>(ops, tr.len, get, sink);
+    }
+  } else {
     bitonic_tile<K>(t, tr.len);
+  }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < tr.len; i += blockDim.x)
     store_elem<K>(ws, 0, tr.start + i, t.get(i));
@@ -194,6 +362,36 @@ __device__ uint32_t merge_path(GetA A, uint32_t na, GetB B, uint32_t nb, uint32_
   return lo;
 }
 
+// The same split found by one warp: each round the 32 lanes test 32 evenly
+// spaced candidates of the remaining range at once (their loads are
+// independent) and the ballot keeps the sub-range where the predicate turns,
+// so a range of r candidates takes about log32(r) rounds of memory latency
+// instead of log2(r).  The predicate "A[i] sorts after B[diag-1-i]" is false
+// then true along i (a strict total order has no ties).  All lanes return the
+// split; every lane of the warp must call.
+template <int K, typename GetA, typename GetB>
+__device__ uint32_t merge_path_warp(GetA A, uint32_t na, GetB B, uint32_t nb, uint32_t diag) {
+  // the split is the first i in [lo, hi] whose predicate holds (i = hi holds
+  // by definition)
+  uint32_t lo = diag > nb ? diag - nb : 0u;
+  uint32_t hi = min(diag, na);
+  const uint32_t lane = threadIdx.x & 31u;
+  while (lo < hi) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t p = lo + lane * step;
+    const bool holds = p >= hi || !elem_less<K>(A(p), B(diag - 1 - p));
+    const uint32_t m = __ballot_sync(0xffffffffu, holds);
+    if (m == 0) {  // every candidate fails: the split lies past the last one
+      lo += 31 * step + 1;
+      continue;
+    }
+    const uint32_t f = __ffs(m) - 1;  // candidate f holds, candidate f-1 fails
+    hi = min(lo + f * step, hi);
+    lo = f ? lo + (f - 1) * step + 1 : lo;
+  }
+  return lo;
+}
+
 // Shared memory of a merge CTA: input then output, each part x (8 KW + 4) bytes.
 __host__ __device__ inline size_t merge_smem_bytes(uint32_t KW, uint32_t part) {
   return 2 * static_cast<size_t>(part) * (8 * KW + 4);
@@ -213,9 +411,11 @@ __device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
   const uint32_t a0 = ps, b0 = ps + na;
   auto gA = [&](uint32_t i) { return src.get(a0 + i); };
   auto gB = [&](uint32_t i) { return src.get(b0 + i); };
-  if (threadIdx.x < 2) {
-    const uint32_t d = (threadIdx.x == 0 ? o0 : o1) - ps;
-    s_split[threadIdx.x] = merge_path<K>(gA, na, gB, nb, d);
+  if (threadIdx.x < 64) {  // warps 0 and 1 find the two splits, 32 candidates a round
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t d = (w == 0 ? o0 : o1) - ps;
+    const uint32_t sp = merge_path_warp<K>(gA, na, gB, nb, d);
+    if ((threadIdx.x & 31u) == 0) s_split[w] = sp;
   }
   __syncthreads();
   const uint32_t i0 = s_split[0], i1 = s_split[1];

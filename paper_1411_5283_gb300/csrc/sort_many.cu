@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(1024) many_tplan_kernel(Many m) {
 
 // A (list, length) bucket of at most `cross` words is sorted whole by
 // odd-even transposition; a larger one by bitonic tiles (merged afterwards).
-__global__ void many_tile_kernel(Many m, uint32_t cross) {
+__global__ void __launch_bounds__(1024) many_tile_kernel(Many m, uint32_t cross) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sm = align128(smem);
   const uint32_t S = m.n_lists * m.W, T = m.T;

@@ -37,7 +37,7 @@ class Request:
     arrival: float = 0.0                     # seconds after the loop started
     rec: object = None                       # numpy array, or a (pinned) CPU tensor
     ln: object = None
-    text: bytes | None = None
+    text: object = None                      # bytes, or a (pinned) uint8 CPU tensor
     max_words: int | None = None             # text mode: word slots to reserve
     # filled by the server
     status: int = -1
@@ -287,7 +287,9 @@ class Server:
                 r.t_launch = t
                 if r.is_text:
                     if len(r.text):
-                        src = torch.frombuffer(bytearray(r.text), dtype=torch.uint8)
+                        # a pinned uint8 tensor is copied asynchronously; bytes are staged
+                        src = r.text if torch.is_tensor(r.text) else \
+                            torch.frombuffer(bytearray(r.text), dtype=torch.uint8)
                         self.text[r.text_off:r.text_off + len(r.text)].copy_(src, non_blocking=True)
                 else:
                     # a pinned CPU tensor is copied asynchronously; a numpy
@@ -355,7 +357,8 @@ class Server:
             if lane.event is not None and lane.event.query():
                 self._complete(lane, release)
         self._admit()
-        self.adm.unblock(any(l.event is not None for l in self.lanes), self.now())
+        busy = any(l.event is not None for l in self.lanes) or self.releases_pending()
+        self.adm.unblock(busy, self.now())
         for lane in self.lanes:
             if lane.event is None and self.admitted:
                 self._launch(lane)
@@ -378,10 +381,18 @@ class Server:
         self._release(req)
 
     # -- driving a trace ----------------------------------------------------------
+    def releases_pending(self) -> bool:
+        """Whether the caller still holds completed requests it will release
+        (then a request that does not fit waits instead of being rejected).
+        A caller that keeps results and frees them later replaces this."""
+        return False
+
     def run_trace(self, requests: list[Request], release: bool = True,
-                  on_done=None) -> dict:
+                  on_done=None, on_step=None) -> dict:
         """Feeds requests at their arrival times (seconds after start) and runs
-        until all are done.  Returns latency and throughput statistics."""
+        until all are done.  on_done(request) runs for every completed
+        request, on_step() once per scheduling round.  Returns latency and
+        throughput statistics."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         self.t0 = time.perf_counter()
         k = 0
@@ -396,6 +407,9 @@ class Server:
                 while seen < len(self.done):
                     on_done(self.done[seen])
                     seen += 1
+            if on_step is not None:
+                on_step()
+            pending = pending or self.releases_pending()
             if k >= len(reqs) and not pending:
                 break
             if k < len(reqs) and not pending:
