@@ -261,12 +261,13 @@ __device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
 __host__ __device__ constexpr uint32_t tile_xslots(uint32_t T) { return T + T / 16; }
 
 // Shared memory of a tile-sort CTA: [mbarrier 16 B][KW key planes of T+2][idx T+4],
-// then the register network's exchange planes (KW key planes and an index
-// plane of tile_xslots(T) slots), plus 128 bytes of slack to align the start.
+// plus 128 bytes of slack to align the start.  The register network (one or
+// two key words) reuses the same area for its exchange planes once the tile
+// is in registers, so the area is the larger of the two.
 __host__ __device__ inline size_t tile_smem_bytes(uint32_t KW, uint32_t T) {
   const size_t planes = static_cast<size_t>(KW) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
-  const size_t xch = static_cast<size_t>(tile_xslots(T)) * (8 * KW + 4);
-  return 128 + 16 + ((planes + 15) & ~size_t(15)) + xch;
+  const size_t xch = static_cast<size_t>(tile_xslots(T)) * (8 * (KW < 2 ? KW : 2) + 4);
+  return 128 + 16 + (planes > xch ? planes : xch);
 }
 
 __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
@@ -316,11 +317,13 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
   const uint32_t E = T / blockDim.x;
   if (odd_even) {
     odd_even_tile<K>(t, tr.len);
-  } else if (T % blockDim.x == 0 && (E == 2 || (E == 4 && K <= 2) || (E == 8 && K == 1))) {
+  } else if (K <= 2 && T % blockDim.x == 0 && (E == 2 || E == 4 || (E == 8 && K == 1))) {
     // bitonic network over registers, E positions per thread; only the
-    // cross-warp steps go through shared memory (one barrier pair each)
-    const size_t planes = static_cast<size_t>(K) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
-    uint8_t* xb = smem + 16 + ((planes + 15) & ~size_t(15));
+    // cross-warp steps go through shared memory (one barrier pair each),
+    // through exchange planes laid over the tile (read into registers before
+    // the first exchange), and the sorted positions go straight to the
+    // workspace from registers
+    uint8_t* xb = smem + 16;
     const uint32_t X = tile_xslots(T);
     SmemTile<K> xt;
 #pragma unroll
@@ -328,13 +331,13 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
     xt.idx = reinterpret_cast<uint32_t*>(xb + static_cast<size_t>(K) * X * 8);
     const ElemOps<K> ops{xt};
     auto get = [&](uint32_t i) { return t.get(i); };
-    auto sink = [&](uint32_t i, const Elem<K>& e) { t.put(i, e); };
-    if (E == 2) {
-      block_sort<ElemOps<K>, 2>(ops, tr.len, get, sink);
-    } else if constexpr (K <= 2) {
-      if (E == 4) block_sort<ElemOps<K>, 4>(ops, tr.len, get, sink);
+    auto sink = [&](uint32_t i, const Elem<K>& e) { store_elem<K>(ws, 0, tr.start + i, e); };
+    if constexpr (K <= 2) {
+      if (E == 2) block_sort<ElemOps<K>, 2>(ops, tr.len, get, sink);
+      else if (E == 4) block_sort<ElemOps<K>, 4>(ops, tr.len, get, sink);
       else if constexpr (K == 1) block_sort<ElemOps<K>, 8>(ops, tr.len, get, sink);
     }
+    return;  // block_sort ends with a barrier; the shared memory is free again
   } else {
     bitonic_tile<K>(t, tr.len);
   }

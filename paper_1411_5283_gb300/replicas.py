@@ -54,3 +54,43 @@ def route(sizes, world: int) -> list[list[int]]:
         out[r].append(i)
         heapq.heappush(heap, (load + int(sizes[i]), r))
     return [sorted(u) for u in out]
+
+
+def shard_lists(sizes, world: int, rank: int):
+    """The lists rank `rank` of `world` sorts (route's share, ascending list
+    ids) and, for the concatenated arrays of all lists, the first word of
+    each: returns (ids, starts) with starts[i] the offset of list i."""
+    import numpy as np
+    sizes = np.asarray(sizes, dtype=np.int64)
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]]) if sizes.size else np.zeros(0, np.int64)
+    return np.asarray(route(sizes, world)[rank], dtype=np.int64), starts
+
+
+def gather_shard(rec, ln, sizes, ids, starts):
+    """This rank's lists, back to back: (rec, len, sizes) of lists `ids`."""
+    import numpy as np
+    W = rec.shape[1]
+    if len(ids) == 0:
+        return np.zeros((0, W), rec.dtype), np.zeros(0, ln.dtype), np.zeros(0, np.int64)
+    parts = [(int(starts[i]), int(sizes[i])) for i in ids]
+    r = np.concatenate([rec[a:a + m] for a, m in parts])
+    l = np.concatenate([ln[a:a + m] for a, m in parts])
+    return r, l, np.asarray([m for _, m in parts], dtype=np.int64)
+
+
+def sort_shard(rec, ln, sizes, world: int, rank: int, W: int, max_list_words: int,
+               alg="merge", tune=None):
+    """Sorts rank `rank`'s share of independent lists (given for the whole
+    batch, concatenated) in one batched call on this rank's GPU; returns
+    (ids, BatchSorter, descriptors) so that list ids[k] is result k."""
+    import torch
+    from . import batch
+    ids, starts = shard_lists(sizes, world, rank)
+    r, l, sz = gather_shard(rec, ln, sizes, ids, starts)
+    desc = batch.record_lists(sz)
+    b = batch.BatchSorter(max(int(l.size), 1), max(len(sz), 1), W)
+    if len(sz):
+        b.set_lists(desc)
+        b.run(torch.from_numpy(r).cuda(), torch.from_numpy(l).cuda(), text=False,
+              max_list_words=max_list_words, alg=alg, tune=tune)
+    return ids, b, desc

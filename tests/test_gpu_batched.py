@@ -169,3 +169,23 @@ def test_crossover_keeps_every_list(env, cross):
     torch.cuda.synchronize()
     for i, (r, l) in enumerate(lists):
         check_list(b, desc, i, r, l, orc)
+
+
+def test_sharded_batch_every_list_matches_oracle(env):
+    """The batch split over two ranks by the host router (each share sorted by
+    its own batched call, here one after the other on this GPU): every list of
+    every share is the oracle's answer for that list."""
+    torch, bs, batch, orc = env
+    from paper_1411_5283_gb300 import replicas
+    W = 16
+    rec, ln, sizes = synth.batch_lists(96, V=50_000, width=W, seed0=900)
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    seen = []
+    for rank in range(2):
+        ids, b, desc = replicas.sort_shard(rec, ln, sizes, 2, rank, W, max_list_words=65_536)
+        torch.cuda.synchronize()
+        for k, i in enumerate(ids):
+            a, z = int(starts[i]), int(starts[i + 1])
+            check_list(b, desc, k, rec[a:z], ln[a:z], orc)
+        seen += list(ids)
+    assert sorted(seen) == list(range(len(sizes)))

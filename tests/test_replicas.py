@@ -76,3 +76,49 @@ def test_route_covers_and_balances(world):
 def test_route_rejects_empty_world():
     with pytest.raises(ValueError):
         replicas.route([1, 2], 0)
+
+
+def _shard_main(rank, world, port, q):
+    """A rank takes its share of a batch of independent lists (the batched
+    workload's generator), builds its concatenated arrays and descriptors,
+    and reports what it would sort; rank 0 collects every rank's share."""
+    import torch.distributed as dist
+    from paper_1411_5283_gb300 import batch, synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rec, ln, sizes = synth.batch_lists(48, V=50_000, width=16, lo=64, hi=4096, seed0=500)
+        ids, starts = replicas.shard_lists(sizes, world, rank)
+        r, l, sz = replicas.gather_shard(rec, ln, sizes, ids, starts)
+        desc = batch.record_lists(sz)
+        # every list of the share is the input's list, at its descriptor's offset
+        ok = all(np.array_equal(r[int(desc["word_off"][k]):int(desc["word_off"][k]) + int(sz[k])],
+                                rec[int(starts[i]):int(starts[i]) + int(sizes[i])])
+                 for k, i in enumerate(ids))
+        shares = [None] * world
+        dist.all_gather_object(shares, (rank, ids.tolist(), int(l.size), ok))
+        if rank == 0:
+            q.put((shares, sizes.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_a_list_batch():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    shares, sizes = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ids = sorted(i for _, share, _, _ in shares for i in share)
+    assert ids == list(range(len(sizes)))                     # every list exactly once
+    assert all(ok for *_, ok in shares)                       # shares hold the right words
+    words = [w for _, _, w, _ in shares]
+    assert sum(words) == sum(sizes)
+    assert max(words) <= sum(sizes) / 2 + max(sizes)          # balanced within one list
