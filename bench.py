@@ -80,6 +80,9 @@ def parse():
                          "calls; served: Poisson requests through the continuous-batching "
                          "server; text: the 240,000-word raw text end to end")
     ap.add_argument("--lists", type=int, default=4096)
+    ap.add_argument("--served-check", choices=["inline", "replay"], default="replay",
+                    help="served: compare every response with the oracle during the timed "
+                         "run (inline) or in an untimed replay of the same trace")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: requests per second")
     ap.add_argument("--profile-run", action="store_true",
@@ -575,14 +578,17 @@ def run_served(args):
         if not group:
             return
         dev_ = torch.device("cuda")
-        ns = torch.tensor([int(r.off[Ws + 1]) if r.status == 0 else 0 for r in group],
-                          dtype=torch.int64, device=dev_)
-        slots = torch.tensor([int(r.slot) for r in group], dtype=torch.int64, device=dev_)
-        es = torch.tensor([int(e_start[r.rid % P]) for r in group], dtype=torch.int64, device=dev_)
         total = int(sum(int(r.off[Ws + 1]) if r.status == 0 else 0 for r in group))
         for r in group:
             check_stream.wait_event(r.ev_end)
+        # every tensor of the check is made and used on the check stream (the
+        # caching allocator then reuses its memory only in that stream's order)
+        meta = torch.tensor([[int(r.off[Ws + 1]) if r.status == 0 else 0 for r in group],
+                             [int(r.slot) for r in group],
+                             [int(e_start[r.rid % P]) for r in group]], dtype=torch.int64).pin_memory()
         with torch.cuda.stream(check_stream):
+            md = meta.to(dev_, non_blocking=True)  # no host wait; the pinned block outlives the copy
+            ns, slots, es = md[0], md[1], md[2]
             if total:
                 which = torch.repeat_interleave(torch.arange(len(group), device=dev_), ns,
                                                 output_size=total)
@@ -619,9 +625,21 @@ def run_served(args):
         retire(False)
 
     srv.releases_pending = lambda: bool(pending or group)
-    stats = srv.run_trace(reqs, release=False, on_done=on_done, on_step=on_step)
-    flush_checks()
-    retire(True)
+    if args.served_check == "inline":
+        stats = srv.run_trace(reqs, release=False, on_done=on_done, on_step=on_step)
+        flush_checks()
+        retire(True)
+    else:
+        stats = srv.run_trace(reqs, release=True)
+    stats["breakdown"] = srv.breakdown()
+    if args.served_check == "replay":
+        # the same trace once more, every response checked (this pass is not timed)
+        srv.done.clear()
+        srv.batches = 0
+        srv.run_trace([request(i, pinned[i % P], float(t[i])) for i in range(len(t))],
+                      release=False, on_done=on_done, on_step=on_step)
+        flush_checks()
+        retire(True)
     torch.cuda.synchronize()
     stats["oracle_checked"] = checked
     stats["oracle_mismatches"] = host_bad + int(bad_dev.item())
@@ -633,8 +651,10 @@ def run_served(args):
                                             "budget_gb": 64, "pool": P},
             "p50_ms": round(stats["p50_ms"], 3), "p99_ms": round(stats["p99_ms"], 3),
             "stats": stats, "cpu_baseline": base,
+            "check": args.served_check,
             "note": "every response is compared with the oracle's answer on the device as it "
-                    "completes (in groups, on a stream of its own, no host sync), inside the run"}
+                    "completes (in groups, on a stream of its own, no host sync), inside the "
+                    "timed run (inline) or in an untimed replay of the same trace (replay)"}
     print(json.dumps(line), flush=True)
 
 

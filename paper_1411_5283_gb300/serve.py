@@ -417,6 +417,27 @@ class Server:
                 time.sleep(min(0.0005, max(0.0, reqs[k].arrival - self.now())))
         return self.stats()
 
+    def breakdown(self) -> dict:
+        """Where the latency goes (ms percentiles): waiting for admission
+        (arrival -> admit), for a lane (admit -> launch), and the batch on the
+        device plus its completion poll (launch -> done); and the sizes of the
+        slowest 1 % of requests."""
+        ok = [r for r in self.done if r.status == 0]
+        if not ok:
+            return {}
+        a = np.array([r.t_admit - r.arrival for r in ok]) * 1e3
+        q = np.array([r.t_launch - r.t_admit for r in ok]) * 1e3
+        d = np.array([r.t_done - r.t_launch for r in ok]) * 1e3
+        lat = np.array([r.latency for r in ok])
+        slow = np.argsort(lat)[-max(1, len(ok) // 100):]
+        pc = lambda x: {"p50": round(float(np.percentile(x, 50)), 3),
+                        "p99": round(float(np.percentile(x, 99)), 3)}
+        return {"admit_wait_ms": pc(a), "lane_wait_ms": pc(q), "run_ms": pc(d),
+                "slowest_1pct_words_median": int(np.median([ok[i].n_slots for i in slow])),
+                "slowest_1pct_text_share": round(float(np.mean([ok[i].is_text for i in slow])), 3),
+                "slowest_1pct_arrival_s": [round(float(np.min([ok[i].arrival for i in slow])), 2),
+                                           round(float(np.max([ok[i].arrival for i in slow])), 2)]}
+
     def stats(self) -> dict:
         ok = [r for r in self.done if r.status == 0]
         lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
