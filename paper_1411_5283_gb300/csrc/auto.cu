@@ -1197,7 +1197,8 @@ __device__ void segsort_big(uint8_t* smem, const AutoView& v, uint32_t seg, uint
 
 // Issues the bulk copies (TMA) of segment seg (c <= capacity) into buffer buf.
 template <int K>
-__device__ void prefetch_segment(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c) {
+__device__ void prefetch_segment(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c,
+                                 bool with_idx = true) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf);
   uint64_t* kp = reinterpret_cast<uint64_t*>(buf + 16);
   const uint32_t C = static_cast<uint32_t>(seg_plane_elems(K));
@@ -1206,12 +1207,12 @@ __device__ void prefetch_segment(uint8_t* buf, const AutoView& v, uint32_t seg, 
   const uint64_t rb = v.rbase[seg], ib = v.ibase[seg];
   // regions start 16-byte aligned (rcap, rbase, ibase are multiples of 4) and
   // hold rcap >= round4(c) elements, so the rounded copies stay inside
-  const uint32_t kbytes = (c * 8 + 15) & ~15u, ibytes = (c * 4 + 15) & ~15u;
+  const uint32_t kbytes = (c * 8 + 15) & ~15u, ibytes = with_idx ? (c * 4 + 15) & ~15u : 0u;
   mbar_arrive_expect_tx(bar, K * kbytes + ibytes);
 #pragma unroll
   for (int k = 0; k < K; ++k)
     bulk_g2s(kp + k * C, v.area64 + rb + static_cast<uint64_t>(k) * rc, kbytes, bar);
-  bulk_g2s(ip, v.area32 + ib, ibytes, bar);
+  if (with_idx) bulk_g2s(ip, v.area32 + ib, ibytes, bar);
 }
 
 __device__ __forceinline__ uint32_t seg_count(const AutoView& v, uint32_t seg) {
@@ -1226,7 +1227,13 @@ __device__ bool maybe_prefetch(uint8_t* buf, const AutoView& v, uint32_t seg, ui
   const uint32_t K = keys_for_len(v.segL[seg]);
   if (c == 0 || c > auto_seg_cap(K)) return false;
   switch (K) {
-    case 1: prefetch_segment<1>(buf, v, seg, c); break;
+    case 1: {
+      // the partition wrote this segment as items (code 2^ib + index) when the
+      // item fits 64 bits: then the index plane was never written
+      const uint32_t* f = v.segf + static_cast<size_t>(seg) * kSegFWords;
+      prefetch_segment<1>(buf, v, seg, c, __ldg(f + 16) + __ldg(f + 17) > 64);
+      break;
+    }
     case 2: prefetch_segment<2>(buf, v, seg, c); break;
     case 3: prefetch_segment<3>(buf, v, seg, c); break;
     default: prefetch_segment<4>(buf, v, seg, c); break;
