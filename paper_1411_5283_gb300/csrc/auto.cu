@@ -1809,8 +1809,10 @@ __device__ __noinline__ void k1_write(uint32_t buf_off, uint32_t idx_off, uint32
 }
 
 // Segments of words with two or more key words (longer than 8 letters, a
-// small share of typical text): bitonic network in shared memory, which keeps
-// no elements in registers.
+// small share of typical text) whose code does not fit the item sort: a
+// bitonic network in shared memory, which keeps no elements in registers.
+// (A register network over (first key word, slot) pairs was measured slower
+// for these segments.)
 template <int K>
 __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c,
                               uint32_t W, uint8_t* out_rec, uint32_t* out_perm) {

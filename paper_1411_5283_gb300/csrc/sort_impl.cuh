@@ -160,13 +160,13 @@ struct ElemOps {
 };
 
 template <typename Ops, int M, int E>
-__device__ __forceinline__ void reg_step(typename Ops::T (&r)[E]) {
+__device__ __forceinline__ void reg_step(typename Ops::T (&r)[E], const Ops& ops) {
   if constexpr (M < E) {
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       constexpr int m = M;
       const int q = j ^ m;
-      if (q > j && Ops::less(r[q], r[j])) {
+      if (q > j && ops.less(r[q], r[j])) {
         const typename Ops::T x = r[j];
         r[j] = r[q];
         r[q] = x;
@@ -184,13 +184,13 @@ __device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops&
   if (mask < E) {
     // in registers: masks are the flips 1, 3, 7, 15 or the cleaners 1, 2, 4, 8
     switch (mask) {
-      case 1: reg_step<Ops, 1, E>(r); break;
-      case 2: reg_step<Ops, 2, E>(r); break;
-      case 3: reg_step<Ops, 3, E>(r); break;
-      case 4: reg_step<Ops, 4, E>(r); break;
-      case 7: reg_step<Ops, 7, E>(r); break;
-      case 8: reg_step<Ops, 8, E>(r); break;
-      default: reg_step<Ops, 15, E>(r); break;
+      case 1: reg_step<Ops, 1, E>(r, ops); break;
+      case 2: reg_step<Ops, 2, E>(r, ops); break;
+      case 3: reg_step<Ops, 3, E>(r, ops); break;
+      case 4: reg_step<Ops, 4, E>(r, ops); break;
+      case 7: reg_step<Ops, 7, E>(r, ops); break;
+      case 8: reg_step<Ops, 8, E>(r, ops); break;
+      default: reg_step<Ops, 15, E>(r, ops); break;
     }
   } else if (lane_mask < 32) {
     // across lanes of one warp; my position is the upper one of its pair when
@@ -202,7 +202,7 @@ __device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops&
 #pragma unroll
       for (int j = 0; j < E; ++j) {
         const T other = Ops::shfl(r[j], lane_mask);
-        if (Ops::less(other, r[j]) == keep_small) r[j] = other;
+        if (ops.less(other, r[j]) == keep_small) r[j] = other;
       }
     } else {
       // flip step (mask = k - 1): slot j pairs with the partner's slot E-1-j.
@@ -212,8 +212,8 @@ __device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops&
       for (int j = 0; j < E / 2; ++j) {
         const T for_j = Ops::shfl(r[E - 1 - j], lane_mask);
         const T for_m = Ops::shfl(r[j], lane_mask);
-        if (Ops::less(for_j, r[j]) == keep_small) r[j] = for_j;
-        if (Ops::less(for_m, r[E - 1 - j]) == keep_small) r[E - 1 - j] = for_m;
+        if (ops.less(for_j, r[j]) == keep_small) r[j] = for_j;
+        if (ops.less(for_m, r[E - 1 - j]) == keep_small) r[E - 1 - j] = for_m;
       }
     }
   } else {
@@ -226,7 +226,7 @@ __device__ __forceinline__ void bitonic_step(typename Ops::T (&r)[E], const Ops&
     for (int j = 0; j < E; ++j) {
       const uint32_t i = tid * E + j, pi = i ^ mask;
       const T other = ops.ld(pi);
-      if (Ops::less(other, r[j]) == (i < pi)) r[j] = other;
+      if (ops.less(other, r[j]) == (i < pi)) r[j] = other;
     }
   }
 }
