@@ -54,7 +54,7 @@ bool bsort::resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, So
   if (p->threads < 64 || p->threads > 1024 || p->threads % 32) return false;
   p->part = t.merge_fanin ? t.merge_fanin : (KW >= 3 ? 1024u : 2048u);
   if (!pow2(p->part) || p->part < 256 || p->part > 4096) return false;
-  if (2ull * p->part * (8 * KW + 4) > 200 * 1024) return false;  // merge CTA shared memory
+  if (2ull * p->part * 12 > 200 * 1024) return false;  // merge CTA shared memory (one-key partitions)
   if (p->part > 2 * p->tile) p->part = 2 * p->tile;  // a partition never spans two run pairs
   if (p->alg == BSORT_ODD_EVEN) {
     p->cross = 0xFFFFFFFFu;  // every tile by odd-even transposition

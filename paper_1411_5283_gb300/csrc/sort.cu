@@ -72,33 +72,40 @@ __global__ void __launch_bounds__(1024) tile_sort_kernel(const uint32_t* __restr
   }
 }
 
-// One merge pass over every bucket longer than R: partition `part`-sized
-// output ranges of each bucket; CTA -> (bucket, partition) by prefix sums.
+// One merge pass over every bucket longer than R: output ranges of each
+// bucket cut into partitions (merge_part_for(part, K) elements, so that one
+// shared-memory size fits every key count), handed to persistent CTAs by a
+// grid-stride loop over the partitions of all buckets.
 __global__ void merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R,
                                   uint32_t part, int src, Ws ws) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ uint32_t s_off[kMaxW + 2];
+  __shared__ uint32_t s_off[kMaxW + 2], s_pre[kMaxW + 2];
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
-  uint32_t acc = 0, L = 0, o0 = 0;
-  for (uint32_t l = 1; l <= W; ++l) {
-    const uint32_t cnt = s_off[l + 1] - s_off[l];
-    if (cnt <= R) continue;
-    const uint32_t np = (cnt + part - 1) / part;
-    if (blockIdx.x < acc + np) {
-      L = l;
-      o0 = (blockIdx.x - acc) * part;
-      break;
+  if (threadIdx.x == 0) {  // partitions of the buckets below L
+    uint32_t acc = 0;
+    for (uint32_t l = 0; l <= W + 1; ++l) {
+      s_pre[l] = acc;
+      if (l >= 1 && l <= W) {
+        const uint32_t cnt = s_off[l + 1] - s_off[l], P = merge_part_for(part, keys_for_len(l));
+        if (cnt > R) acc += (cnt + P - 1) / P;
+      }
     }
-    acc += np;
   }
-  if (L == 0) return;
-  const uint32_t bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
-  switch (keys_for_len(L)) {
-    case 1: merge_partition<1>(smem, part, bstart, cnt, R, o0, src, ws); break;
-    case 2: merge_partition<2>(smem, part, bstart, cnt, R, o0, src, ws); break;
-    case 3: merge_partition<3>(smem, part, bstart, cnt, R, o0, src, ws); break;
-    default: merge_partition<4>(smem, part, bstart, cnt, R, o0, src, ws); break;
+  __syncthreads();
+  const uint32_t total = s_pre[W + 1];
+  uint32_t L = 1;
+  for (uint32_t q = blockIdx.x; q < total; q += gridDim.x) {
+    while (L < W && s_pre[L + 1] <= q) ++L;  // block-uniform; a CTA's partitions increase
+    const uint32_t K = keys_for_len(L), P = merge_part_for(part, K);
+    const uint32_t o0 = (q - s_pre[L]) * P;
+    const uint32_t bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
+    switch (K) {
+      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, ws); break;
+      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, ws); break;
+      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, ws); break;
+      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, ws); break;
+    }
   }
 }
 
@@ -111,14 +118,19 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   const size_t tsm = tile_smem_bytes(KW, T);
   static SmemOptIn tile_smem_set, merge_smem_set;
   const uint32_t part = p.part;
-  const size_t msm = merge_smem_bytes(KW, part);
+  const size_t msm = merge_smem_bytes(1, part);  // partitions shrink with the key count
   cudaError_t e = ensure_smem(tile_sort_kernel, tsm, &tile_smem_set);
   if (e == cudaSuccess) e = ensure_smem(merge_pass_kernel, msm, &merge_smem_set);
   if (e != cudaSuccess) return e;
   const uint32_t tiles = (n_cap + T - 1) / T + W;
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "tile_odd_even" : "tile_bitonic", tile_sort_kernel, tiles,
                p.threads, tsm, s, d_off, W, T, p.cross, ws);
-  const uint32_t parts = (n_cap + part - 1) / part + W;
+  // persistent merge CTAs: as many as fit the SMs (shared memory, 256 threads)
+  const uint32_t per_sm = static_cast<uint32_t>((200 * 1024) / (msm + 1024)) < 8
+                              ? static_cast<uint32_t>((200 * 1024) / (msm + 1024)) : 8u;
+  const uint32_t need = (n_cap + part - 1) / part * 4 + W;  // partitions are at most part / 4
+  const uint32_t fit = static_cast<uint32_t>(device_sm_count()) * (per_sm ? per_sm : 1u);
+  const uint32_t parts = need < fit ? need : fit;
   int src = 0;
   for (uint64_t R = T; R < n_cap; R <<= 1) {
     BSORT_LAUNCH("merge_pass", merge_pass_kernel, parts, 256, msm, s, d_off, W,

@@ -400,6 +400,15 @@ __host__ __device__ inline size_t merge_smem_bytes(uint32_t KW, uint32_t part) {
   return 2 * static_cast<size_t>(part) * (8 * KW + 4);
 }
 
+// Elements per merge partition for elements of K key words when one-key
+// partitions hold `part`: wider elements take smaller partitions, so that a
+// merge CTA's shared memory (merge_smem_bytes(1, part)) fits every K and is
+// sized for the common one-key words rather than the widest (2 K + 1 words
+// per element against 3: halved for two keys, quartered for three or four).
+__host__ __device__ constexpr uint32_t merge_part_for(uint32_t part, uint32_t K) {
+  return K <= 1 ? part : K == 2 ? part / 2 : part / 4;
+}
+
 // Merges output range [o0, min(o0 + part, cnt)) of one merge pass: runs of
 // length R at src (planes of a bucket or segment, cnt elements) are merged in
 // pairs into dst.  part must divide 2R.  smem holds 2 x part elements.

@@ -168,20 +168,51 @@ __device__ __forceinline__ uint32_t upper_index(const uint32_t* a, uint32_t n, u
 // Exclusive scan of f(0..n-1) by one block into out[0..n]; returns the total.
 template <typename F>
 __device__ uint32_t block_scan_into(uint32_t n, F f, uint32_t* out) {
+  // chunks of kScanChunk values: read with coalesced accesses (all of a
+  // thread's reads in flight together) into shared memory, scanned there,
+  // written back coalesced; a running carry joins the chunks
+  constexpr uint32_t kScanChunk = 8192;
+  constexpr uint32_t kPer = kScanChunk / 1024;
   __shared__ uint32_t tmp[1024 / 32 + 1];
-  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-  const uint32_t b = threadIdx.x * per, e = min(n, b + per);
-  uint32_t s = 0;
-  for (uint32_t i = b; i < e; ++i) s += f(i);
-  uint32_t tot;
-  uint32_t run = block_exclusive_scan(s, tmp, &tot);
-  for (uint32_t i = b; i < e; ++i) {
-    const uint32_t v = f(i);
-    out[i] = run;
-    run += v;
+  __shared__ uint32_t chunk[kScanChunk];
+  uint32_t carry = 0;
+  for (uint32_t c0 = 0; c0 < n; c0 += kScanChunk) {
+    const uint32_t m = min(kScanChunk, n - c0);
+    uint32_t vals[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = k * blockDim.x + threadIdx.x;
+      vals[k] = i < m ? f(c0 + i) : 0u;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = k * blockDim.x + threadIdx.x;
+      if (i < kScanChunk) chunk[i] = vals[k];
+    }
+    __syncthreads();
+    // thread t scans positions t kPer .. t kPer + kPer - 1 of the chunk
+    uint32_t mine[kPer], s = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x * kPer + k;
+      mine[k] = i < kScanChunk ? chunk[i] : 0u;
+      s += mine[k];
+    }
+    uint32_t tot;
+    uint32_t run = carry + block_exclusive_scan(s, tmp, &tot);
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x * kPer + k;
+      if (i < kScanChunk) chunk[i] = run;
+      run += mine[k];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) out[c0 + i] = chunk[i];
+    carry += tot;
+    __syncthreads();  // the chunk is reused
   }
-  if (threadIdx.x == 0) out[n] = tot;
-  return tot;
+  if (threadIdx.x == 0) out[n] = carry;
+  return carry;
 }
 
 __device__ __forceinline__ const uint8_t* len_of(const Many& m, const uint8_t* len, int text) {
@@ -455,11 +486,11 @@ __global__ void __launch_bounds__(1024) many_tile_kernel(Many m, uint32_t cross)
 }
 
 __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m, uint32_t R) {
-  const uint32_t S = m.n_lists * m.W, P = m.part;
+  const uint32_t S = m.n_lists * m.W;
   const uint32_t tot = block_scan_into(
       S,
       [&](uint32_t s) {
-        const uint32_t c = m.seg_cnt[s];
+        const uint32_t c = m.seg_cnt[s], P = merge_part_for(m.part, keys_for_len(s % m.W + 1));
         return c > R ? (c + P - 1) / P : 0u;
       },
       m.part_pre);
@@ -468,11 +499,12 @@ __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m, uint32_t R) {
 
 __global__ void many_merge_kernel(Many m, uint32_t R, int src) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const uint32_t S = m.n_lists * m.W, P = m.part;
+  const uint32_t S = m.n_lists * m.W;
   const uint32_t parts = m.hdr->parts;
   for (uint32_t p = blockIdx.x; p < parts; p += gridDim.x) {
     const uint32_t s = upper_index(m.part_pre, S + 1, p);
     const uint32_t L = s % m.W + 1;
+    const uint32_t P = merge_part_for(m.part, keys_for_len(L));
     const uint32_t o0 = (p - m.part_pre[s]) * P;
     const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
     switch (keys_for_len(L)) {
@@ -557,7 +589,7 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   m.T = p.tile;
   m.part = p.part;
   const uint32_t KW = W / 8;
-  const size_t tsm = tile_smem_bytes(KW, p.tile), msm = merge_smem_bytes(KW, p.part);
+  const size_t tsm = tile_smem_bytes(KW, p.tile), msm = merge_smem_bytes(1, p.part);
   static SmemOptIn tile_set, merge_set;
   cudaError_t e = ensure_smem(many_tile_kernel, tsm, &tile_set);
   if (e == cudaSuccess) e = ensure_smem(many_merge_kernel, msm, &merge_set);
