@@ -430,7 +430,13 @@ __device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
     if ((threadIdx.x & 31u) == 0) s_split[w] = sp;
   }
   __syncthreads();
-  const uint32_t i0 = s_split[0], i1 = s_split[1];
+  // Sorted runs give i0 <= i1 <= i0 + (o1 - o0).  After a device error (a tile
+  // left unsorted) the splits may disagree; clamping i1 into that range keeps
+  // every access below inside the two runs and the shared tiles (the output
+  // is then undefined, as the error status says).
+  const uint32_t i0 = s_split[0];
+  const uint32_t e1 = o1 - ps, lo1 = e1 > nb ? e1 - nb : 0u;
+  const uint32_t i1 = min(max(s_split[1], max(i0, lo1)), min(i0 + (o1 - o0), na));
   const uint32_t j0 = (o0 - ps) - i0, j1 = (o1 - ps) - i1;
   const uint32_t ca = i1 - i0, cb = j1 - j0, tot = ca + cb;
   // smem: input tile (A part then B part), output tile

@@ -104,7 +104,11 @@ __device__ void merge_range(uint8_t* smem, const uint8_t* src_rec, const uint32_
   if (threadIdx.x < 2)
     s_split[threadIdx.x] = split_global<KW>(src_rec, g0, na, g0 + na, nb, threadIdx.x == 0 ? d0 : d1);
   __syncthreads();
-  const uint32_t i0 = s_split[0], i1 = s_split[1];
+  // sorted runs give i0 <= i1 <= i0 + (d1 - d0); clamping keeps every access
+  // inside the runs should an earlier error have left them unsorted
+  const uint32_t i0 = s_split[0];
+  const uint32_t lo1 = d1 > nb ? d1 - nb : 0u;
+  const uint32_t i1 = min(max(s_split[1], max(i0, lo1)), min(i0 + (d1 - d0), na));
   const uint32_t j0 = d0 - i0, j1 = d1 - i1;
   const uint32_t ca = i1 - i0, cb = j1 - j0, tot = ca + cb;
   RecTile<KW> in, out;
