@@ -453,11 +453,97 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
   }
 }
 
+// (list, length) buckets of at most kWarpSortMax words are sorted by one warp
+// each (many_small_kernel); the tile kernel takes the larger ones.
+constexpr uint32_t kWarpSortMax = 64;
+
 __global__ void __launch_bounds__(1024) many_tplan_kernel(Many m) {
   const uint32_t S = m.n_lists * m.W, T = m.T;
   const uint32_t tot = block_scan_into(
-      S, [&](uint32_t s) { return (m.seg_cnt[s] + T - 1) / T; }, m.tile_pre);
+      S,
+      [&](uint32_t s) {
+        const uint32_t c = m.seg_cnt[s];
+        return c <= kWarpSortMax ? 0u : (c + T - 1) / T;
+      },
+      m.tile_pre);
   if (threadIdx.x == 0) m.hdr->tiles = tot;
+}
+
+// One warp sorts one small bucket in registers, two positions per lane
+// (positions 2l and 2l + 1 in lane l), with no block barrier: by odd-even
+// transposition (the even phase compares a lane's own pair, the odd phase
+// its second position with the next lane's first; two quiet phases in a row
+// end it) when the bucket has at most `cross` words, else by a bitonic
+// network over shuffles.  Many warps of a CTA sort different buckets at once.
+template <int K>
+__device__ void warp_sort_small(Many& m, uint32_t start, uint32_t cnt, uint32_t cross) {
+  const uint32_t lane = lane_id();
+  Elem<K> r[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint32_t p = 2 * lane + j;
+    r[j] = p < cnt ? load_elem<K>(m.ws, 0, start + p) : elem_inf<K>();
+  }
+  if (cnt <= cross) {
+    bool prev_quiet = false;
+    for (uint32_t ph = 0; ph < cnt; ++ph) {
+      bool swapped = false;
+      if ((ph & 1u) == 0) {
+        if (elem_less<K>(r[1], r[0])) {
+          const Elem<K> x = r[0];
+          r[0] = r[1];
+          r[1] = x;
+          swapped = true;
+        }
+      } else {
+        // r[1] of lane l against r[0] of lane l + 1 (the last lane's r[1] has no partner)
+        Elem<K> up, down;
+        up.idx = __shfl_down_sync(0xffffffffu, r[0].idx, 1);
+        down.idx = __shfl_up_sync(0xffffffffu, r[1].idx, 1);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          up.k[k] = __shfl_down_sync(0xffffffffu, r[0].k[k], 1);
+          down.k[k] = __shfl_up_sync(0xffffffffu, r[1].k[k], 1);
+        }
+        if (lane < 31 && elem_less<K>(up, r[1])) {
+          r[1] = up;
+          swapped = true;
+        }
+        if (lane > 0 && elem_less<K>(r[0], down)) r[0] = down;
+      }
+      const bool quiet = !__any_sync(0xffffffffu, swapped);
+      if (quiet && prev_quiet) break;
+      prev_quiet = quiet;
+    }
+  } else {
+    SmemTile<K> none{};  // the network below never leaves the warp
+    const ElemOps<K> ops{none};
+    for (uint32_t k = 2; k <= 64; k <<= 1) {  // 64 positions: two per lane
+      bitonic_step<ElemOps<K>, 2>(r, ops, k - 1);
+      for (uint32_t j = k >> 2; j > 0; j >>= 1) bitonic_step<ElemOps<K>, 2>(r, ops, j);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint32_t p = 2 * lane + j;
+    if (p < cnt) store_elem<K>(m.ws, 0, start + p, r[j]);
+  }
+}
+
+__global__ void __launch_bounds__(256) many_small_kernel(Many m, uint32_t cross) {
+  const uint32_t S = m.n_lists * m.W;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t s = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); s < S; s += warps) {
+    const uint32_t cnt = m.seg_cnt[s];  // warp-uniform
+    if (cnt < 2 || cnt > kWarpSortMax) continue;
+    const uint32_t start = m.seg_start[s];
+    switch (keys_for_len(s % m.W + 1)) {
+      case 1: warp_sort_small<1>(m, start, cnt, cross); break;
+      case 2: warp_sort_small<2>(m, start, cnt, cross); break;
+      case 3: warp_sort_small<3>(m, start, cnt, cross); break;
+      default: warp_sort_small<4>(m, start, cnt, cross); break;
+    }
+  }
 }
 
 // A (list, length) bucket of at most `cross` words is sorted whole by
@@ -602,6 +688,7 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   BSORT_LAUNCH("many_lscan", many_lscan_kernel, grid, kThreads, 0, s, m, out_off);
   BSORT_LAUNCH("many_scatter", many_scatter_kernel, grid, kThreads, 0, s, text_or_rec, len, text, m);
   BSORT_LAUNCH("many_tplan", many_tplan_kernel, 1, 1024, 0, s, m);
+  BSORT_LAUNCH("many_small", many_small_kernel, grid, 256, 0, s, m, p.cross);
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "many_tile_odd_even" : "many_tile_bitonic", many_tile_kernel,
                grid, p.threads, tsm, s, m, p.cross);
   int src = 0;
