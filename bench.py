@@ -74,11 +74,14 @@ def parse():
     ap.add_argument("--alg", default="auto")
     ap.add_argument("--words", type=int, default=N_WORDS)
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["large", "batched", "served", "text"], default="large",
+    ap.add_argument("--workload", choices=["large", "batched", "served", "text", "whole", "packed"],
+                    default="large",
                     help="large: 16.7M pre-tokenised words (default, the headline line); "
                          "batched: 4,096 lists in one graph-captured batched call vs per-list "
                          "calls; served: Poisson requests through the continuous-batching "
-                         "server; text: the 240,000-word raw text end to end")
+                         "server; text: the 240,000-word raw text end to end; whole: the "
+                         "unbucketed order of the large table; packed: the large table's answer "
+                         "as packed bytes plus offsets")
     ap.add_argument("--lists", type=int, default=4096)
     ap.add_argument("--served-check", choices=["inline", "replay"], default="replay",
                     help="served: compare every response with the oracle during the timed "
@@ -658,6 +661,63 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_variant(args):
+    """The large table through the paper's other two forms: `whole` is the
+    unbucketed order (Table 2, second row: every word by its bytes), `packed`
+    the bucketed order written as packed bytes plus offsets (the "vectors of
+    string" of §3.1).  One step = one call of each form's path."""
+    import torch
+
+    import paper_1411_5283_gb300 as bs
+    from paper_1411_5283_gb300 import synth
+    bs._lib.load()
+    n = args.words
+    rec_np, len_np = synth.large_records(SEED, n, W)
+    rec, ln = torch.from_numpy(rec_np).cuda(), torch.from_numpy(len_np).cuda()
+    s = bs.Sorter(n, W)
+    out_bytes = torch.empty(n * W, dtype=torch.uint8, device="cuda")
+    if args.workload == "whole":
+        def step():
+            s.sort_records_whole(rec, ln, n, alg=args.alg)
+    else:
+        def step():
+            s.sort_records(rec, ln, n, alg=args.alg)
+            s.pack(n, bucketed=True, out_bytes=out_bytes)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if args.profile_run:
+        print(json.dumps({"profile_run": True, "workload": args.workload, "ms_per_step": ms}), flush=True)
+        return
+    bs.bsort_profile_reset()
+    bs.bsort_profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    bs.bsort_profile_enable(False)
+    prof = bs.bsort_profile_read()
+    total_bytes = int(len_np.astype(np.int64).sum())
+    line = {"metric": f"Mwords/s sorted, {args.workload} form", "value": round(n / ms / 1e3, 2),
+            "unit": "Mwords/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD}", "alg": args.alg},
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()}}
+    if args.workload == "packed":
+        line["packed_output_bytes_per_word"] = round((total_bytes + 4 * (n + 1) + 4 * n) / n, 2)
+        line["record_output_bytes_per_word"] = W + 4
+    print(json.dumps(line), flush=True)
+
+
 def run_text(args):
     """Raw text end to end (tokenise, bucket, sort, gather in one call): the
     32,768-word text of seed 0 (vocabulary 4,500) and the 240,000-word text of
@@ -720,6 +780,8 @@ def main():
         return run_batched(args)
     if args.workload == "text":
         return run_text(args)
+    if args.workload in ("whole", "packed"):
+        return run_variant(args)
     if args.workload == "served":
         return run_served(args)
     rank = int(os.environ.get("RANK", 0))
