@@ -37,7 +37,7 @@ static_assert(sizeof(WsHeader) <= 4096, "header too large");
 constexpr uint32_t kWsMagic = 0x42534f52u;
 
 struct WsLayout {
-  size_t header, table, keys_a, keys_b, keys_c, idx_a, idx_b, idx_c, misc, autoa, total;
+  size_t header, table, keys_a, keys_b, keys_c, idx_a, idx_b, idx_c, misc, splits, autoa, total;
   uint64_t cap;       // element capacity of each plane (>= max_words + 64)
   uint32_t K;         // key planes
 };
@@ -118,6 +118,10 @@ constexpr WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
   o += align_up(4 * third, 256);
   l.misc = o;
   o += 64 * 1024;
+  // merge-path splits of one merge pass: two per partition, partitions of at
+  // least 64 elements (the smallest partition of the widest words)
+  l.splits = o;
+  o += align_up(4 * 2 * (cap / 64 + 2 * static_cast<size_t>(kBins)), 256);
   l.autoa = o;
   o += auto_bytes(cap, W);
   l.total = o;
@@ -161,6 +165,7 @@ struct Ws {
   uint32_t* table;
   uint8_t* autoa;     // sample-sort area (samples, splitters, segment tables)
   uint32_t* misc;     // 64 KB of small per-call state (e.g. internal bucket offsets)
+  uint32_t* splits;   // merge-path splits of the current merge pass
   uint64_t* keys[2];
   uint32_t* idx[2];
   uint64_t cap;
@@ -180,6 +185,7 @@ inline Ws ws_view(const void* base, size_t ws_bytes, uint32_t W) {
   w.idx[1] = reinterpret_cast<uint32_t*>(b + l.idx_b);
   w.autoa = reinterpret_cast<uint8_t*>(b + l.autoa);
   w.misc = reinterpret_cast<uint32_t*>(b + l.misc);
+  w.splits = reinterpret_cast<uint32_t*>(b + l.splits);
   w.cap = l.cap;
   w.K = l.K;
   w.wait_polls = first_wait_polls();

@@ -72,6 +72,49 @@ __global__ void __launch_bounds__(1024) tile_sort_kernel(const uint32_t* __restr
   }
 }
 
+// Partitions of one merge pass over every bucket longer than R (prefix over
+// the buckets in s_pre; thread 0 writes it).
+__device__ void pass_partitions(const uint32_t* s_off, uint32_t W, uint32_t R, uint32_t part, uint32_t* s_pre) {
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (uint32_t l = 0; l <= W + 1; ++l) {
+      s_pre[l] = acc;
+      if (l >= 1 && l <= W) {
+        const uint32_t cnt = s_off[l + 1] - s_off[l], P = merge_part_for(part, keys_for_len(l));
+        if (cnt > R) acc += (cnt + P - 1) / P;
+      }
+    }
+  }
+}
+
+// The splits of every partition of one merge pass, one warp per partition
+// (all partitions' searches at once, instead of each merge CTA waiting for
+// its own): splits[2q], splits[2q + 1] for partition q.
+__global__ void __launch_bounds__(256)
+merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, uint32_t part, int src,
+                   Ws ws) {
+  __shared__ uint32_t s_off[kMaxW + 2], s_pre[kMaxW + 2];
+  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
+  __syncthreads();
+  pass_partitions(s_off, W, R, part, s_pre);
+  __syncthreads();
+  const uint32_t total = s_pre[W + 1];
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t q = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); q < total; q += warps) {
+    uint32_t L = 1;
+    while (L < W && s_pre[L + 1] <= q) ++L;  // warp-uniform
+    const uint32_t K = keys_for_len(L), P = merge_part_for(part, K);
+    const uint32_t o0 = (q - s_pre[L]) * P, bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
+    uint32_t* out = ws.splits + 2 * static_cast<size_t>(q);
+    switch (K) {
+      case 1: merge_splits_warp<1>(P, bstart, cnt, R, o0, src, ws, out); break;
+      case 2: merge_splits_warp<2>(P, bstart, cnt, R, o0, src, ws, out); break;
+      case 3: merge_splits_warp<3>(P, bstart, cnt, R, o0, src, ws, out); break;
+      default: merge_splits_warp<4>(P, bstart, cnt, R, o0, src, ws, out); break;
+    }
+  }
+}
+
 // One merge pass over every bucket longer than R: output ranges of each
 // bucket cut into partitions (merge_part_for(part, K) elements, so that one
 // shared-memory size fits every key count), handed to persistent CTAs by a
@@ -82,16 +125,7 @@ __global__ void merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W
   __shared__ uint32_t s_off[kMaxW + 2], s_pre[kMaxW + 2];
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) {  // partitions of the buckets below L
-    uint32_t acc = 0;
-    for (uint32_t l = 0; l <= W + 1; ++l) {
-      s_pre[l] = acc;
-      if (l >= 1 && l <= W) {
-        const uint32_t cnt = s_off[l + 1] - s_off[l], P = merge_part_for(part, keys_for_len(l));
-        if (cnt > R) acc += (cnt + P - 1) / P;
-      }
-    }
-  }
+  pass_partitions(s_off, W, R, part, s_pre);
   __syncthreads();
   const uint32_t total = s_pre[W + 1];
   uint32_t L = 1;
@@ -100,11 +134,12 @@ __global__ void merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W
     const uint32_t K = keys_for_len(L), P = merge_part_for(part, K);
     const uint32_t o0 = (q - s_pre[L]) * P;
     const uint32_t bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
+    const uint32_t* pre = ws.splits + 2 * static_cast<size_t>(q);
     switch (K) {
-      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, ws); break;
-      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, ws); break;
-      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, ws); break;
-      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, ws); break;
+      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
+      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
+      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
+      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
     }
   }
 }
@@ -132,7 +167,11 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   const uint32_t fit = static_cast<uint32_t>(device_sm_count()) * (per_sm ? per_sm : 1u);
   const uint32_t parts = need < fit ? need : fit;
   int src = 0;
+  const uint32_t split_ctas = (need + 7) / 8 < static_cast<uint32_t>(device_sm_count()) * 8
+                                  ? (need + 7) / 8 : static_cast<uint32_t>(device_sm_count()) * 8;
   for (uint64_t R = T; R < n_cap; R <<= 1) {
+    BSORT_LAUNCH("merge_split", merge_split_kernel, split_ctas, 256, 0, s, d_off, W,
+                 static_cast<uint32_t>(R), part, src, ws);
     BSORT_LAUNCH("merge_pass", merge_pass_kernel, parts, 256, msm, s, d_off, W,
                  static_cast<uint32_t>(R), part, src, ws);
     src ^= 1;

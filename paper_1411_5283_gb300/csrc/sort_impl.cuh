@@ -414,7 +414,8 @@ __host__ __device__ constexpr uint32_t merge_part_for(uint32_t part, uint32_t K)
 // pairs into dst.  part must divide 2R.  smem holds 2 x part elements.
 template <int K>
 __device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
-                           const SmemTile<K>& dst, uint32_t cnt, uint32_t R, uint32_t o0) {
+                           const SmemTile<K>& dst, uint32_t cnt, uint32_t R, uint32_t o0,
+                           const uint32_t* pre = nullptr) {
   __shared__ uint32_t s_split[2];
   const uint32_t o1 = min(o0 + part, cnt);
   const uint32_t ps = o0 / (2 * R) * (2 * R);
@@ -423,7 +424,9 @@ __device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
   const uint32_t a0 = ps, b0 = ps + na;
   auto gA = [&](uint32_t i) { return src.get(a0 + i); };
   auto gB = [&](uint32_t i) { return src.get(b0 + i); };
-  if (threadIdx.x < 64) {  // warps 0 and 1 find the two splits, 32 candidates a round
+  if (pre) {  // found beforehand by merge_split_kernel
+    if (threadIdx.x < 2) s_split[threadIdx.x] = pre[threadIdx.x];
+  } else if (threadIdx.x < 64) {  // warps 0 and 1 find the two splits, 32 candidates a round
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t d = (w == 0 ? o0 : o1) - ps;
     const uint32_t sp = merge_path_warp<K>(gA, na, gB, nb, d);
@@ -482,9 +485,30 @@ __device__ __forceinline__ SmemTile<K> ws_planes(const Ws& ws, int buf, uint64_t
 
 template <int K>
 __device__ void merge_partition(uint8_t* smem, uint32_t part, uint32_t bstart, uint32_t cnt,
-                                uint32_t R, uint32_t o0, int src, const Ws& ws) {
+                                uint32_t R, uint32_t o0, int src, const Ws& ws,
+                                const uint32_t* pre = nullptr) {
   merge_tile<K>(smem, part, ws_planes<K>(ws, src, bstart), ws_planes<K>(ws, src ^ 1, bstart), cnt,
-                R, o0);
+                R, o0, pre);
+}
+
+// The two splits (elements of the first run among the outputs before the
+// partition's first and past its last output) of partition [o0, o0 + part)
+// of a bucket's merge pass, found by one warp.
+template <int K>
+__device__ void merge_splits_warp(uint32_t part, uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o0,
+                                  int src, const Ws& ws, uint32_t* out) {
+  const SmemTile<K> t = ws_planes<K>(ws, src, bstart);
+  const uint32_t o1 = min(o0 + part, cnt);
+  const uint32_t ps = o0 / (2 * R) * (2 * R);
+  const uint32_t na = min(R, cnt - ps), nb = min(R, cnt - ps - na);
+  auto gA = [&](uint32_t i) { return t.get(ps + i); };
+  auto gB = [&](uint32_t i) { return t.get(ps + na + i); };
+  const uint32_t s0 = merge_path_warp<K>(gA, na, gB, nb, o0 - ps);
+  const uint32_t s1 = merge_path_warp<K>(gA, na, gB, nb, o1 - ps);
+  if ((threadIdx.x & 31u) == 0) {
+    out[0] = s0;
+    out[1] = s1;
+  }
 }
 
 }  // namespace bsort

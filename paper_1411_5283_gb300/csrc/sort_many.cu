@@ -46,7 +46,7 @@ struct ManyHdr {
 
 // Workspace of bsort_sort_many, a pure function of (cap, W, n_lists).
 struct ManyLayout {
-  size_t header, lists, item_start, segs, seg_cnt, tile_pre, part_pre, table, keys_a, keys_b,
+  size_t header, lists, item_start, segs, seg_cnt, tile_pre, part_pre, splits, table, keys_a, keys_b,
       idx_a, idx_b, trec, tlen, total;
   uint64_t cap, items_max;
 };
@@ -72,6 +72,10 @@ constexpr ManyLayout many_layout_cap(uint64_t cap, uint32_t W, uint32_t n_lists)
   o += align_up(4 * (S + 1), 256);
   l.part_pre = o;
   o += align_up(4 * (S + 1), 256);
+  // merge-path splits of one pass: two per partition (at least 64 elements
+  // each, plus one partial partition per segment)
+  l.splits = o;
+  o += align_up(4 * 2 * (cap / 64 + S + 1), 256);
   l.table = o;
   o += align_up(4 * l.items_max * (W + 1), 256);
   l.keys_a = o;
@@ -139,6 +143,7 @@ Many many_view(void* base, size_t ws_bytes, uint32_t W, uint32_t n_lists, const 
   m.ws.wait_polls = first_wait_polls();
   m.ws.hdr = reinterpret_cast<WsHeader*>(b + l.header + 256);
   m.ws.table = m.table;
+  m.ws.splits = reinterpret_cast<uint32_t*>(b + l.splits);
   m.ws.autoa = nullptr;
   m.ws.keys[0] = reinterpret_cast<uint64_t*>(b + l.keys_a);
   m.ws.keys[1] = reinterpret_cast<uint64_t*>(b + l.keys_b);
@@ -583,6 +588,27 @@ __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m, uint32_t R) {
   if (threadIdx.x == 0) m.hdr->parts = tot;
 }
 
+// The splits of every partition of one merge pass, one warp per partition.
+__global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t R, int src) {
+  const uint32_t S = m.n_lists * m.W;
+  const uint32_t parts = m.hdr->parts;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t p = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); p < parts; p += warps) {
+    const uint32_t s = upper_index(m.part_pre, S + 1, p);
+    const uint32_t L = s % m.W + 1;
+    const uint32_t P = merge_part_for(m.part, keys_for_len(L));
+    const uint32_t o0 = (p - m.part_pre[s]) * P;
+    const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
+    uint32_t* out = m.ws.splits + 2 * static_cast<size_t>(p);
+    switch (keys_for_len(L)) {
+      case 1: merge_splits_warp<1>(P, bstart, cnt, R, o0, src, m.ws, out); break;
+      case 2: merge_splits_warp<2>(P, bstart, cnt, R, o0, src, m.ws, out); break;
+      case 3: merge_splits_warp<3>(P, bstart, cnt, R, o0, src, m.ws, out); break;
+      default: merge_splits_warp<4>(P, bstart, cnt, R, o0, src, m.ws, out); break;
+    }
+  }
+}
+
 __global__ void many_merge_kernel(Many m, uint32_t R, int src) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t S = m.n_lists * m.W;
@@ -593,11 +619,12 @@ __global__ void many_merge_kernel(Many m, uint32_t R, int src) {
     const uint32_t P = merge_part_for(m.part, keys_for_len(L));
     const uint32_t o0 = (p - m.part_pre[s]) * P;
     const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
+    const uint32_t* pre = m.ws.splits + 2 * static_cast<size_t>(p);
     switch (keys_for_len(L)) {
-      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, m.ws); break;
-      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, m.ws); break;
-      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, m.ws); break;
-      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, m.ws); break;
+      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
+      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
+      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
+      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
     }
   }
 }
@@ -694,6 +721,7 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   int src = 0;
   for (uint64_t R = p.tile; R < max_list_words; R <<= 1) {
     BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m, static_cast<uint32_t>(R));
+    BSORT_LAUNCH("many_split", many_split_kernel, grid * 2, 256, 0, s, m, static_cast<uint32_t>(R), src);
     BSORT_LAUNCH("many_merge", many_merge_kernel, grid, 256, msm, s, m, static_cast<uint32_t>(R), src);
     src ^= 1;
   }
