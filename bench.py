@@ -40,15 +40,16 @@ NCU_TRAFFIC = {
     # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
-    "auto_segsort": {"bytes": 4 * (76.73e6 + 126.32e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "052163496737",
-                                 "paper_1411_5283_gb300/csrc/common.cuh": "74c36b14a4c1"}},
-    "auto_partition": {"bytes": 4 * (55.02e6 + 2.41e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "052163496737",
-                                   "paper_1411_5283_gb300/csrc/common.cuh": "74c36b14a4c1"}},
-    "auto_bucket": {"bytes": 4 * (139.03e6 + 26.08e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "052163496737",
-                                "paper_1411_5283_gb300/csrc/common.cuh": "74c36b14a4c1"}},
+    "auto_segsort": {"bytes": 4 * (60.69e6 + 126.21e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "f70b5c4f2307",
+                                 "paper_1411_5283_gb300/csrc/common.cuh": "e41e15ea3b9c",
+                                 "paper_1411_5283_gb300/csrc/sort_impl.cuh": "17574389fb25"}},
+    "auto_partition": {"bytes": 4 * (27.57e6 + 1.22e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "f70b5c4f2307",
+                                   "paper_1411_5283_gb300/csrc/common.cuh": "e41e15ea3b9c"}},
+    "auto_bucket": {"bytes": 4 * (138.94e6 + 23.28e6),
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "f70b5c4f2307",
+                                "paper_1411_5283_gb300/csrc/common.cuh": "e41e15ea3b9c"}},
 }
 
 

@@ -64,20 +64,35 @@ __device__ __forceinline__ bool key_less(const uint64_t (&a)[KW], const uint64_t
   return false;
 }
 
-// Number of elements of run A among the first d outputs of the stable merge
-// of A (na records at a) and B (nb records at b), equal records taken from A
-// first: the largest i with A[i-1] not after B[d-i].
+// Splits: the number of elements of run A among the first d outputs of the
+// stable merge of A (na records at a) and B (nb records at b), equal records
+// taken from A first.
+// The same split found by one warp, 32 candidates a round: the predicate "A[i]
+// comes after B[d-1-i]" is false then true along i (merge_path_warp's scheme;
+// every lane of the warp calls and gets the split).
 template <int KW>
-__device__ uint32_t split_global(const uint8_t* rec, uint64_t a, uint32_t na, uint64_t b, uint32_t nb,
-                                 uint32_t d) {
+__device__ uint32_t split_global_warp(const uint8_t* rec, uint64_t a, uint32_t na, uint64_t b, uint32_t nb,
+                                      uint32_t d) {
   uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
+  const uint32_t lane = threadIdx.x & 31u;
   while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    uint64_t ka[KW], kb[KW];
-    load_key<KW>(rec, a + mid, ka);
-    load_key<KW>(rec, b + d - 1 - mid, kb);
-    if (!key_less<KW>(kb, ka)) lo = mid + 1;  // A[mid] comes first: it is among the first d
-    else hi = mid;
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t q = lo + lane * step;
+    bool holds = q >= hi;
+    if (!holds) {
+      uint64_t ka[KW], kb[KW];
+      load_key<KW>(rec, a + q, ka);
+      load_key<KW>(rec, b + d - 1 - q, kb);
+      holds = key_less<KW>(kb, ka);
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, holds);
+    if (m == 0) {
+      lo += 31 * step + 1;
+      continue;
+    }
+    const uint32_t f = __ffs(m) - 1;
+    hi = min(lo + f * step, hi);
+    lo = f ? lo + (f - 1) * step + 1 : lo;
   }
   return lo;
 }
@@ -101,8 +116,11 @@ __device__ void merge_range(uint8_t* smem, const uint8_t* src_rec, const uint32_
                             uint8_t* dst_rec, uint32_t* dst_perm, uint64_t g0, uint32_t na,
                             uint32_t nb, uint32_t d0, uint32_t d1) {
   __shared__ uint32_t s_split[2];
-  if (threadIdx.x < 2)
-    s_split[threadIdx.x] = split_global<KW>(src_rec, g0, na, g0 + na, nb, threadIdx.x == 0 ? d0 : d1);
+  if (threadIdx.x < 64) {  // warps 0 and 1: the two splits
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t sp = split_global_warp<KW>(src_rec, g0, na, g0 + na, nb, w == 0 ? d0 : d1);
+    if ((threadIdx.x & 31u) == 0) s_split[w] = sp;
+  }
   __syncthreads();
   // sorted runs give i0 <= i1 <= i0 + (d1 - d0); clamping keeps every access
   // inside the runs should an earlier error have left them unsorted
