@@ -283,6 +283,29 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / k2, dev)
+    # the same, with the answer in the packed "vectors of string" form
+    total_bytes = int(len_np.astype(np.int64).sum())
+    outs_p = [(torch.empty(max(total_bytes, 16), dtype=torch.uint8).pin_memory(),
+               torch.empty(n + 1, dtype=torch.int32).pin_memory(),
+               torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(depth)]
+
+    def e2e_packed_run(k):
+        pipe.start_after()
+        for j in range(k):
+            o = outs_p[j % depth]
+            pipe.submit_packed(rec_h, len_h, n, total_bytes, o[0], o[1], o[2], alg=args.alg)
+        pipe.wait_all()
+
+    e2e_packed_run(depth)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0.record(stream)
+    e2e_packed_run(k2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_packed_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / k2, dev)
+    d2h_packed = total_bytes + 4 * (n + 1) + 4 * n
     del pipe
 
     # ---- roofline of the dominant kernel ----------------------------------
@@ -305,7 +328,8 @@ def run_ours(args, rank, world, local_rank):
     out_rec_np = s.out_rec[:n].cpu().numpy()
     return {
         "out": (out_rec_np, out_perm_np, off, len_np),
-        "ms": ms, "e2e_ms": e2e_ms, "n": n, "prof": prof, "clk": clk,
+        "ms": ms, "e2e_ms": e2e_ms, "e2e_packed_ms": e2e_packed_ms, "d2h_packed": d2h_packed,
+        "n": n, "prof": prof, "clk": clk,
         "roofline": {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(name), "peak_kind": peak_kind,
@@ -815,6 +839,12 @@ def main():
                     "ms_per_step": round(r["e2e_ms"], 4),
                     "how": "pinned host table in, answer out, every step; consecutive steps "
                            "on two streams (HostPipeline) so copies and sorts overlap"},
+            "e2e_packed": {"value": round(replicas.throughput(n_total, r["e2e_packed_ms"]), 2),
+                           "unit": "Mwords/s", "h2d_bytes_per_step": r["h2d"],
+                           "d2h_bytes_per_step": r["d2h_packed"],
+                           "ms_per_step": round(r["e2e_packed_ms"], 4),
+                           "how": "as e2e, the answer read back as packed bytes + offsets[n+1] + "
+                                  "permutation (the paper's vectors-of-string form)"},
             "roofline": r["roofline"],
             "path_roofline": r["path_roofline"],
             "gpu_launches": r["gpu_launches"],

@@ -57,6 +57,31 @@ class HostPipeline:
         s["done"] = ev
         return ev
 
+    def submit_packed(self, rec_h, len_h, n: int, total_bytes: int, bytes_h, offsets_h, out_perm_h,
+                      alg="auto", tune=None):
+        """As submit, but the answer comes back in the paper's "vectors of
+        string" form (§3.1): the sorted words packed without padding
+        (total_bytes = the sum of the input lengths, known to the caller) plus
+        offsets[n + 1], and the permutation."""
+        torch = self.torch
+        s = self.slots[self.k % self.depth]
+        self.k += 1
+        if "bytes" not in s:
+            s["bytes"] = torch.empty(max(self.max_words * self.W, 16), dtype=torch.uint8,
+                                     device=s["rec"].device)
+        with torch.cuda.stream(s["stream"]):
+            s["rec"][:n].copy_(rec_h[:n], non_blocking=True)
+            s["len"][:n].copy_(len_h[:n], non_blocking=True)
+            out_rec, out_perm, off = s["sorter"].sort_records(s["rec"], s["len"], n, alg=alg, tune=tune)
+            b, offsets = s["sorter"].pack(n, bucketed=True, out_bytes=s["bytes"])
+            bytes_h[:total_bytes].copy_(b[:total_bytes], non_blocking=True)
+            offsets_h[:n + 1].copy_(offsets, non_blocking=True)
+            out_perm_h[:n].copy_(out_perm, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s["stream"])
+        s["done"] = ev
+        return ev
+
     def wait_all(self, stream=None):
         """Makes `stream` (default: the current stream) wait for every queued job."""
         torch = self.torch

@@ -35,3 +35,31 @@ def test_pipelined_jobs_match_oracle(orc):
         assert np.array_equal(o_off.numpy().view(np.uint32), want.off)
         assert np.array_equal(o_perm.numpy().view(np.uint32), want.out_perm)
         assert np.array_equal(o_rec.numpy(), want.out_rec)
+
+
+def test_pipelined_packed_jobs_match_oracle(orc):
+    """The same pipeline with answers read back as packed bytes, offsets and
+    the permutation: each job equals the oracle's answer packed by the
+    oracle."""
+    torch = need_cuda()
+    from paper_1411_5283_gb300.pipeline import HostPipeline
+    W = 32
+    jobs = [synth.large_records(51, 120_000, W), table(52, 3_000, W), synth.large_records(53, 70_000, W)]
+    pipe = HostPipeline(120_000, W, depth=2)
+    outs = []
+    pipe.start_after()
+    for rec, ln in jobs:
+        n, total = ln.size, int(ln.astype(np.int64).sum())
+        o = (torch.empty(total, dtype=torch.uint8).pin_memory(), torch.empty(n + 1, dtype=torch.int32).pin_memory(),
+             torch.empty(n, dtype=torch.int32).pin_memory())
+        pipe.submit_packed(torch.from_numpy(rec).pin_memory(), torch.from_numpy(ln).pin_memory(), n, total, *o)
+        outs.append(o)
+    pipe.wait_all()
+    torch.cuda.synchronize()
+    assert pipe.status() == 0
+    for (rec, ln), (o_bytes, o_off, o_perm) in zip(jobs, outs):
+        want = orc.stable_sort(orc.Words(rec, ln))
+        want_bytes, want_off = orc.pack_words(want.out_rec, ln[want.out_perm])
+        assert np.array_equal(o_perm.numpy().view(np.uint32), want.out_perm)
+        assert np.array_equal(o_off.numpy().view(np.uint32), want_off)
+        assert np.array_equal(o_bytes.numpy(), want_bytes)
