@@ -87,9 +87,9 @@ __device__ void pass_partitions(const uint32_t* s_off, uint32_t W, uint32_t R, u
   }
 }
 
-// The splits of every partition of one merge pass, one warp per partition
+// The split of every partition of one merge pass, one warp per partition
 // (all partitions' searches at once, instead of each merge CTA waiting for
-// its own): splits[2q], splits[2q + 1] for partition q.
+// its own): splits[q] for partition q.
 __global__ void __launch_bounds__(256)
 merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, uint32_t part, int src,
                    Ws ws) {
@@ -105,12 +105,12 @@ merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, u
     while (L < W && s_pre[L + 1] <= q) ++L;  // warp-uniform
     const uint32_t K = keys_for_len(L), P = merge_part_for(part, K);
     const uint32_t o0 = (q - s_pre[L]) * P, bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
-    uint32_t* out = ws.splits + 2 * static_cast<size_t>(q);
+    uint32_t* out = ws.splits + q;
     switch (K) {
-      case 1: merge_splits_warp<1>(P, bstart, cnt, R, o0, src, ws, out); break;
-      case 2: merge_splits_warp<2>(P, bstart, cnt, R, o0, src, ws, out); break;
-      case 3: merge_splits_warp<3>(P, bstart, cnt, R, o0, src, ws, out); break;
-      default: merge_splits_warp<4>(P, bstart, cnt, R, o0, src, ws, out); break;
+      case 1: merge_split_warp<1>(bstart, cnt, R, o0, src, ws, out); break;
+      case 2: merge_split_warp<2>(bstart, cnt, R, o0, src, ws, out); break;
+      case 3: merge_split_warp<3>(bstart, cnt, R, o0, src, ws, out); break;
+      default: merge_split_warp<4>(bstart, cnt, R, o0, src, ws, out); break;
     }
   }
 }
@@ -118,30 +118,29 @@ merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, u
 // One merge pass over every bucket longer than R: output ranges of each
 // bucket cut into partitions (merge_part_for(part, K) elements, so that one
 // shared-memory size fits every key count), handed to persistent CTAs by a
-// grid-stride loop over the partitions of all buckets.
-__global__ void merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R,
-                                  uint32_t part, int src, Ws ws) {
-  extern __shared__ __align__(16) uint8_t smem[];
+// grid-stride loop over the partitions of all buckets, each CTA's inputs
+// staged by bulk copies one partition ahead (merge_pass_staged).
+__global__ void __launch_bounds__(256) merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W,
+                                                           uint32_t R, uint32_t part, int src, Ws ws) {
+  extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2], s_pre[kMaxW + 2];
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();
   pass_partitions(s_off, W, R, part, s_pre);
   __syncthreads();
   const uint32_t total = s_pre[W + 1];
+  // thread 0 walks its partitions in increasing order, so the length search
+  // only moves forward
   uint32_t L = 1;
-  for (uint32_t q = blockIdx.x; q < total; q += gridDim.x) {
-    while (L < W && s_pre[L + 1] <= q) ++L;  // block-uniform; a CTA's partitions increase
-    const uint32_t K = keys_for_len(L), P = merge_part_for(part, K);
-    const uint32_t o0 = (q - s_pre[L]) * P;
-    const uint32_t bstart = s_off[L], cnt = s_off[L + 1] - s_off[L];
-    const uint32_t* pre = ws.splits + 2 * static_cast<size_t>(q);
-    switch (K) {
-      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
-      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
-      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
-      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, ws, pre); break;
-    }
-  }
+  const auto part_of = [&](uint32_t q, uint32_t* K, uint32_t* P, uint32_t* bstart, uint32_t* cnt, uint32_t* o0) {
+    while (L < W && s_pre[L + 1] <= q) ++L;
+    *K = keys_for_len(L);
+    *P = merge_part_for(part, *K);
+    *o0 = (q - s_pre[L]) * *P;
+    *bstart = s_off[L];
+    *cnt = s_off[L + 1] - s_off[L];
+  };
+  merge_pass_staged(align128(smem), part, total, R, src, ws, part_of);
 }
 
 }  // namespace
@@ -153,7 +152,7 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   const size_t tsm = tile_smem_bytes(KW, T);
   static SmemOptIn tile_smem_set, merge_smem_set;
   const uint32_t part = p.part;
-  const size_t msm = merge_smem_bytes(1, part);  // partitions shrink with the key count
+  const size_t msm = merge_staged_smem_bytes(part) + 128;  // partitions shrink with the key count
   cudaError_t e = ensure_smem(tile_sort_kernel, tsm, &tile_smem_set);
   if (e == cudaSuccess) e = ensure_smem(merge_pass_kernel, msm, &merge_smem_set);
   if (e != cudaSuccess) return e;
@@ -161,10 +160,12 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "tile_odd_even" : "tile_bitonic", tile_sort_kernel, tiles,
                p.threads, tsm, s, d_off, W, T, p.cross, ws);
   // persistent merge CTAs: as many as fit the SMs (shared memory, 256 threads)
-  const uint32_t per_sm = static_cast<uint32_t>((200 * 1024) / (msm + 1024)) < 8
-                              ? static_cast<uint32_t>((200 * 1024) / (msm + 1024)) : 8u;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, merge_pass_kernel, 256, msm);
+  if (e != cudaSuccess) return e;
+  const uint32_t per_sm = occ < 1 ? 1u : occ > 8 ? 8u : static_cast<uint32_t>(occ);
   const uint32_t need = (n_cap + part - 1) / part * 4 + W;  // partitions are at most part / 4
-  const uint32_t fit = static_cast<uint32_t>(device_sm_count()) * (per_sm ? per_sm : 1u);
+  const uint32_t fit = static_cast<uint32_t>(device_sm_count()) * per_sm;
   const uint32_t parts = need < fit ? need : fit;
   int src = 0;
   const uint32_t split_ctas = (need + 7) / 8 < static_cast<uint32_t>(device_sm_count()) * 8

@@ -395,14 +395,9 @@ __device__ uint32_t merge_path_warp(GetA A, uint32_t na, GetB B, uint32_t nb, ui
   return lo;
 }
 
-// Shared memory of a merge CTA: input then output, each part x (8 KW + 4) bytes.
-__host__ __device__ inline size_t merge_smem_bytes(uint32_t KW, uint32_t part) {
-  return 2 * static_cast<size_t>(part) * (8 * KW + 4);
-}
-
 // Elements per merge partition for elements of K key words when one-key
 // partitions hold `part`: wider elements take smaller partitions, so that a
-// merge CTA's shared memory (merge_smem_bytes(1, part)) fits every K and is
+// merge CTA's shared memory (merge_staged_smem_bytes(part)) fits every K and is
 // sized for the common one-key words rather than the widest (2 K + 1 words
 // per element against 3: halved for two keys, quartered for three or four).
 __host__ __device__ constexpr uint32_t merge_part_for(uint32_t part, uint32_t K) {
@@ -414,8 +409,7 @@ __host__ __device__ constexpr uint32_t merge_part_for(uint32_t part, uint32_t K)
 // pairs into dst.  part must divide 2R.  smem holds 2 x part elements.
 template <int K>
 __device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
-                           const SmemTile<K>& dst, uint32_t cnt, uint32_t R, uint32_t o0,
-                           const uint32_t* pre = nullptr) {
+                           const SmemTile<K>& dst, uint32_t cnt, uint32_t R, uint32_t o0) {
   __shared__ uint32_t s_split[2];
   const uint32_t o1 = min(o0 + part, cnt);
   const uint32_t ps = o0 / (2 * R) * (2 * R);
@@ -424,9 +418,7 @@ __device__ void merge_tile(uint8_t* smem, uint32_t part, const SmemTile<K>& src,
   const uint32_t a0 = ps, b0 = ps + na;
   auto gA = [&](uint32_t i) { return src.get(a0 + i); };
   auto gB = [&](uint32_t i) { return src.get(b0 + i); };
-  if (pre) {  // found beforehand by merge_split_kernel
-    if (threadIdx.x < 2) s_split[threadIdx.x] = pre[threadIdx.x];
-  } else if (threadIdx.x < 64) {  // warps 0 and 1 find the two splits, 32 candidates a round
+  if (threadIdx.x < 64) {  // warps 0 and 1 find the two splits, 32 candidates a round
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t d = (w == 0 ? o0 : o1) - ps;
     const uint32_t sp = merge_path_warp<K>(gA, na, gB, nb, d);
@@ -483,32 +475,215 @@ __device__ __forceinline__ SmemTile<K> ws_planes(const Ws& ws, int buf, uint64_t
   return t;
 }
 
+// The split of partition [o0, o0 + part) of a bucket's merge pass: how many
+// of its first o0 - ps outputs come from the first run of its pair (ps the
+// pair's start), found by one warp.  The partition's end split is the next
+// partition's split, or the whole first run at the pair's end.
 template <int K>
-__device__ void merge_partition(uint8_t* smem, uint32_t part, uint32_t bstart, uint32_t cnt,
-                                uint32_t R, uint32_t o0, int src, const Ws& ws,
-                                const uint32_t* pre = nullptr) {
-  merge_tile<K>(smem, part, ws_planes<K>(ws, src, bstart), ws_planes<K>(ws, src ^ 1, bstart), cnt,
-                R, o0, pre);
-}
-
-// The two splits (elements of the first run among the outputs before the
-// partition's first and past its last output) of partition [o0, o0 + part)
-// of a bucket's merge pass, found by one warp.
-template <int K>
-__device__ void merge_splits_warp(uint32_t part, uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o0,
-                                  int src, const Ws& ws, uint32_t* out) {
+__device__ void merge_split_warp(uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o0, int src,
+                                 const Ws& ws, uint32_t* out) {
   const SmemTile<K> t = ws_planes<K>(ws, src, bstart);
-  const uint32_t o1 = min(o0 + part, cnt);
   const uint32_t ps = o0 / (2 * R) * (2 * R);
   const uint32_t na = min(R, cnt - ps), nb = min(R, cnt - ps - na);
   auto gA = [&](uint32_t i) { return t.get(ps + i); };
   auto gB = [&](uint32_t i) { return t.get(ps + na + i); };
-  const uint32_t s0 = merge_path_warp<K>(gA, na, gB, nb, o0 - ps);
-  const uint32_t s1 = merge_path_warp<K>(gA, na, gB, nb, o1 - ps);
-  if ((threadIdx.x & 31u) == 0) {
-    out[0] = s0;
-    out[1] = s1;
+  const uint32_t s0 = o0 == ps ? 0u : merge_path_warp<K>(gA, na, gB, nb, o0 - ps);
+  if ((threadIdx.x & 31u) == 0) *out = s0;
+}
+
+// ---------------------------------------------------------------------------
+// Merge pass with bulk-copy staging, two input buffers per CTA
+// ---------------------------------------------------------------------------
+// A persistent CTA takes partitions q, q + G, q + 2G, ... of one merge pass.
+// While it merges partition q from one shared-memory buffer, the bulk-copy
+// (TMA) engine already fills the other with partition q + G's two input ranges
+// (one copy per key plane and index plane of each run), their splits coming
+// from merge_split_kernel.  The merged partition goes to a third buffer and
+// from there to global memory in coalesced stores.
+//
+// Input buffer layout for elements of K key words and partitions of P
+// elements: [mbarrier 16 B][K key planes of P + 32 slots][index plane of
+// P + 32 slots].  In each plane the first run's range starts at the plane's
+// start and the second's at the next 16-byte boundary after it; a range is
+// copied from the 16-byte boundary at or below its first element (up to 1 key
+// or 3 indices of slack), so element i of a range sits at (shift + i).
+struct MergeGeo {
+  uint32_t K, P, ca, cb;
+  uint64_t out0;              // first output position (bucket start + o0)
+  uint32_t aA, aB, aAi, aBi;  // element shifts of the two ranges in the key / index planes
+  uint32_t bB, bBi;           // byte offset of the second range in a key / index plane
+};
+
+// One input buffer (a multiple of 128 bytes): the layout above for the
+// largest K x P product (one key word and `part` elements; wider elements
+// take smaller partitions, merge_part_for).
+__host__ __device__ constexpr size_t merge_buf_bytes(uint32_t part) {
+  return (16 + static_cast<size_t>(part + 32) * 12 + 512 + 127) / 128 * 128;
+}
+
+// The output buffer: K key planes and an index plane of P elements.
+__host__ __device__ constexpr size_t merge_out_bytes(uint32_t part) {
+  return (static_cast<size_t>(part) * 12 + 127) / 128 * 128;
+}
+
+// Shared memory of a staged merge CTA.
+__host__ __device__ constexpr size_t merge_staged_smem_bytes(uint32_t part) {
+  return 2 * merge_buf_bytes(part) + merge_out_bytes(part);
+}
+
+__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// Thread 0: the geometry of partition [o0, o0 + P) of a pass over runs of R
+// of a bucket (cnt elements at bstart of buffer src) whose raw splits are s0
+// and s1; issues the partition's bulk copies into buf, whose barrier is told
+// the bytes to expect.
+__device__ inline MergeGeo merge_issue(uint8_t* buf, uint32_t K, uint32_t P, uint32_t bstart, uint32_t cnt,
+                                       uint32_t o0, uint32_t R, int src, const Ws& ws, uint32_t s0,
+                                       uint32_t s1) {
+  MergeGeo g;
+  g.K = K;
+  g.P = P;
+  const uint32_t o1 = min(o0 + P, cnt);
+  const uint32_t ps = o0 / (2 * R) * (2 * R);
+  const uint32_t na = min(R, cnt - ps), nb = min(R, cnt - ps - na);
+  const uint32_t d0 = o0 - ps, d1 = o1 - ps;
+  // Sorted runs give max(0, d0 - nb) <= i0 <= min(na, d0) and
+  // max(i0, d1 - nb) <= i1 <= min(na, i0 + d1 - d0).  Clamping the splits into
+  // those ranges keeps every copy inside the two runs and the buffer when a
+  // device error left a run unsorted (the output is then undefined, as the
+  // error status says).
+  const uint32_t i0 = min(max(s0, d0 > nb ? d0 - nb : 0u), min(na, d0));
+  const uint32_t i1 = min(max(s1, max(i0, d1 > nb ? d1 - nb : 0u)), min(na, i0 + (d1 - d0)));
+  const uint32_t j0 = d0 - i0;
+  g.ca = i1 - i0;
+  g.cb = (d1 - d0) - g.ca;
+  g.out0 = static_cast<uint64_t>(bstart) + o0;
+  const uint64_t gA = static_cast<uint64_t>(bstart) + ps + i0, gB = static_cast<uint64_t>(bstart) + ps + na + j0;
+  g.aA = static_cast<uint32_t>(gA & 1u);
+  g.aB = static_cast<uint32_t>(gB & 1u);
+  g.aAi = static_cast<uint32_t>(gA & 3u);
+  g.aBi = static_cast<uint32_t>(gB & 3u);
+  // plane capacities cover the rounding: (a + c) 8 rounded up stays within
+  // (P + 32) 8 for both ranges together, and likewise for the indices; the
+  // planes hold cap >= n + 64 elements, so no copy reads past one
+  const uint32_t kbA = g.ca ? round16((g.aA + g.ca) * 8) : 0u, kbB = g.cb ? round16((g.aB + g.cb) * 8) : 0u;
+  const uint32_t ibA = g.ca ? round16((g.aAi + g.ca) * 4) : 0u, ibB = g.cb ? round16((g.aBi + g.cb) * 4) : 0u;
+  g.bB = kbA;
+  g.bBi = ibA;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf);
+  const uint32_t ks = (P + 32) * 8;
+  uint8_t* ib = buf + 16 + K * ks;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bar, K * (kbA + kbB) + ibA + ibB);
+  for (uint32_t k = 0; k < K; ++k) {
+    const uint64_t* plane = ws.keys[src] + static_cast<uint64_t>(k) * ws.cap;
+    uint8_t* kb = buf + 16 + k * ks;
+    if (kbA) bulk_g2s(kb, plane + (gA - g.aA), kbA, bar);
+    if (kbB) bulk_g2s(kb + kbA, plane + (gB - g.aB), kbB, bar);
   }
+  if (ibA) bulk_g2s(ib, ws.idx[src] + (gA - g.aAi), ibA, bar);
+  if (ibB) bulk_g2s(ib + ibA, ws.idx[src] + (gB - g.aBi), ibB, bar);
+  return g;
+}
+
+// Merges a staged partition into `out` (thread t produces outputs
+// [t per, t per + per)), then writes it to buffer src ^ 1 in coalesced stores.
+template <int K>
+__device__ void merge_staged(const uint8_t* buf, uint8_t* out, const MergeGeo& g, int src, const Ws& ws) {
+  const uint32_t ks = (g.P + 32) * 8;
+  const uint8_t* ibase = buf + 16 + K * ks;
+  const auto A = [&](uint32_t i) {
+    Elem<K> e;
+#pragma unroll
+    for (int k = 0; k < K; ++k) e.k[k] = reinterpret_cast<const uint64_t*>(buf + 16 + k * ks)[g.aA + i];
+    e.idx = reinterpret_cast<const uint32_t*>(ibase)[g.aAi + i];
+    return e;
+  };
+  const auto B = [&](uint32_t i) {
+    Elem<K> e;
+#pragma unroll
+    for (int k = 0; k < K; ++k) e.k[k] = reinterpret_cast<const uint64_t*>(buf + 16 + k * ks + g.bB)[g.aB + i];
+    e.idx = reinterpret_cast<const uint32_t*>(ibase + g.bBi)[g.aBi + i];
+    return e;
+  };
+  SmemTile<K> o;
+#pragma unroll
+  for (int k = 0; k < K; ++k) o.k[k] = reinterpret_cast<uint64_t*>(out) + k * g.P;
+  o.idx = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(out) + K * g.P);
+  const uint32_t tot = g.ca + g.cb;
+  const uint32_t per = (g.P + blockDim.x - 1) / blockDim.x;
+  const uint32_t d0 = min(tot, threadIdx.x * per), d1 = min(tot, d0 + per);
+  uint32_t ia = merge_path<K>(A, g.ca, B, g.cb, d0), ib = d0 - ia;
+  // the two heads stay in registers; only the side taken is read again
+  Elem<K> a = ia < g.ca ? A(ia) : elem_inf<K>(), b = ib < g.cb ? B(ib) : elem_inf<K>();
+  for (uint32_t d = d0; d < d1; ++d) {
+    const bool takeA = ib >= g.cb || (ia < g.ca && elem_less<K>(a, b));
+    o.put(d, takeA ? a : b);
+    if (takeA) {
+      if (++ia < g.ca) a = A(ia);
+    } else {
+      if (++ib < g.cb) b = B(ib);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x) store_elem<K>(ws, src ^ 1, g.out0 + i, o.get(i));
+}
+
+// One merge pass over `total` partitions; part_of(q, &K, &P, &bstart, &cnt,
+// &o0) describes partition q, whose split (merge_split_warp) is ws.splits[q].
+// Partitions of one bucket are numbered consecutively, so partition q's end
+// split is ws.splits[q + 1] unless q ends its run pair.
+// smem (128-byte aligned) holds merge_staged_smem_bytes(part).  Returns false
+// (with the status set) when a wait gave up; the copies in flight have then
+// landed (or their wait gave up too).
+template <typename PartOf>
+__device__ bool merge_pass_staged(uint8_t* smem, uint32_t part, uint32_t total, uint32_t R, int src,
+                                  const Ws& ws, PartOf part_of) {
+  __shared__ MergeGeo s_geo[2];
+  uint8_t* buf[2] = {smem, smem + merge_buf_bytes(part)};
+  uint8_t* out = smem + 2 * merge_buf_bytes(part);
+  if (threadIdx.x == 0) {
+    mbar_init(reinterpret_cast<uint64_t*>(buf[0]), 1);
+    mbar_init(reinterpret_cast<uint64_t*>(buf[1]), 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t phase[2] = {0u, 0u};
+  bool pending[2] = {false, false};  // thread 0: a copy is in flight into buffer x
+  const auto issue = [&](uint32_t q, int x) {
+    uint32_t K, P, bstart, cnt, o0;
+    part_of(q, &K, &P, &bstart, &cnt, &o0);
+    const uint32_t o1 = min(o0 + P, cnt), ps = o0 / (2 * R) * (2 * R);
+    const uint32_t s1 = o1 - ps == min(2 * R, cnt - ps) ? min(R, cnt - ps) : ws.splits[q + 1];
+    s_geo[x] = merge_issue(buf[x], K, P, bstart, cnt, o0, R, src, ws, ws.splits[q], s1);
+    pending[x] = true;
+  };
+  int b = 0;
+  if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x, 0);
+  for (uint32_t q = blockIdx.x; q < total; q += gridDim.x, b ^= 1) {
+    const uint32_t qn = q + gridDim.x;
+    if (threadIdx.x == 0 && qn < total) issue(qn, b ^ 1);  // buffer b ^ 1 was released last round
+    const bool ok = mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf[b]), phase[b], ws.wait_polls);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        set_error(ws.hdr, BSORT_E_TIMEOUT);
+        for (int x = 0; x < 2; ++x)  // let the copies in flight land before the CTA exits
+          if (pending[x]) mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf[x]), phase[x]);
+      }
+      return false;
+    }
+    phase[b] ^= 1u;
+    pending[b] = false;
+    const MergeGeo g = s_geo[b];
+    switch (g.K) {
+      case 1: merge_staged<1>(buf[b], out, g, src, ws); break;
+      case 2: merge_staged<2>(buf[b], out, g, src, ws); break;
+      case 3: merge_staged<3>(buf[b], out, g, src, ws); break;
+      default: merge_staged<4>(buf[b], out, g, src, ws); break;
+    }
+    __syncthreads();  // buffer b, its geometry and the output buffer are free again
+  }
+  return true;
 }
 
 }  // namespace bsort

@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m, uint32_t R) {
   if (threadIdx.x == 0) m.hdr->parts = tot;
 }
 
-// The splits of every partition of one merge pass, one warp per partition.
+// The split of every partition of one merge pass, one warp per partition.
 __global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t R, int src) {
   const uint32_t S = m.n_lists * m.W;
   const uint32_t parts = m.hdr->parts;
@@ -599,34 +599,31 @@ __global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t R, int
     const uint32_t P = merge_part_for(m.part, keys_for_len(L));
     const uint32_t o0 = (p - m.part_pre[s]) * P;
     const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
-    uint32_t* out = m.ws.splits + 2 * static_cast<size_t>(p);
+    uint32_t* out = m.ws.splits + p;
     switch (keys_for_len(L)) {
-      case 1: merge_splits_warp<1>(P, bstart, cnt, R, o0, src, m.ws, out); break;
-      case 2: merge_splits_warp<2>(P, bstart, cnt, R, o0, src, m.ws, out); break;
-      case 3: merge_splits_warp<3>(P, bstart, cnt, R, o0, src, m.ws, out); break;
-      default: merge_splits_warp<4>(P, bstart, cnt, R, o0, src, m.ws, out); break;
+      case 1: merge_split_warp<1>(bstart, cnt, R, o0, src, m.ws, out); break;
+      case 2: merge_split_warp<2>(bstart, cnt, R, o0, src, m.ws, out); break;
+      case 3: merge_split_warp<3>(bstart, cnt, R, o0, src, m.ws, out); break;
+      default: merge_split_warp<4>(bstart, cnt, R, o0, src, m.ws, out); break;
     }
   }
 }
 
-__global__ void many_merge_kernel(Many m, uint32_t R, int src) {
-  extern __shared__ __align__(16) uint8_t smem[];
+// One merge pass over the partitions of every segment longer than R, each
+// persistent CTA's inputs staged by bulk copies one partition ahead
+// (merge_pass_staged).
+__global__ void __launch_bounds__(256) many_merge_kernel(Many m, uint32_t R, int src) {
+  extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t S = m.n_lists * m.W;
-  const uint32_t parts = m.hdr->parts;
-  for (uint32_t p = blockIdx.x; p < parts; p += gridDim.x) {
+  const auto part_of = [&](uint32_t p, uint32_t* K, uint32_t* P, uint32_t* bstart, uint32_t* cnt, uint32_t* o0) {
     const uint32_t s = upper_index(m.part_pre, S + 1, p);
-    const uint32_t L = s % m.W + 1;
-    const uint32_t P = merge_part_for(m.part, keys_for_len(L));
-    const uint32_t o0 = (p - m.part_pre[s]) * P;
-    const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
-    const uint32_t* pre = m.ws.splits + 2 * static_cast<size_t>(p);
-    switch (keys_for_len(L)) {
-      case 1: merge_partition<1>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
-      case 2: merge_partition<2>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
-      case 3: merge_partition<3>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
-      default: merge_partition<4>(smem, P, bstart, cnt, R, o0, src, m.ws, pre); break;
-    }
-  }
+    *K = keys_for_len(s % m.W + 1);
+    *P = merge_part_for(m.part, *K);
+    *o0 = (p - m.part_pre[s]) * *P;
+    *bstart = m.seg_start[s];
+    *cnt = m.seg_cnt[s];
+  };
+  merge_pass_staged(align128(smem), m.part, m.hdr->parts, R, src, m.ws, part_of);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -702,12 +699,18 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   m.T = p.tile;
   m.part = p.part;
   const uint32_t KW = W / 8;
-  const size_t tsm = tile_smem_bytes(KW, p.tile), msm = merge_smem_bytes(1, p.part);
+  const size_t tsm = tile_smem_bytes(KW, p.tile);
+  const size_t msm = merge_staged_smem_bytes(p.part) + 128;
   static SmemOptIn tile_set, merge_set;
   cudaError_t e = ensure_smem(many_tile_kernel, tsm, &tile_set);
   if (e == cudaSuccess) e = ensure_smem(many_merge_kernel, msm, &merge_set);
   if (e != cudaSuccess) return e;
   const uint32_t grid = static_cast<uint32_t>(sms) * 4;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, many_merge_kernel, 256, msm);
+  if (e != cudaSuccess) return e;
+  // persistent merge CTAs: as many as fit the SMs
+  const uint32_t mgrid = static_cast<uint32_t>(sms) * (occ < 1 ? 1u : occ > 8 ? 8u : static_cast<uint32_t>(occ));
   BSORT_LAUNCH("many_init", many_init_kernel, 1, 1024, 0, s, m, text);
   if (text) BSORT_LAUNCH("many_tokenize", many_tok_kernel, grid, kTokThreads, 0, s, text_or_rec, m);
   BSORT_LAUNCH("many_plan", many_plan_kernel, 1, 1024, 0, s, m, max_list_words);
@@ -722,7 +725,7 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   for (uint64_t R = p.tile; R < max_list_words; R <<= 1) {
     BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m, static_cast<uint32_t>(R));
     BSORT_LAUNCH("many_split", many_split_kernel, grid * 2, 256, 0, s, m, static_cast<uint32_t>(R), src);
-    BSORT_LAUNCH("many_merge", many_merge_kernel, grid, 256, msm, s, m, static_cast<uint32_t>(R), src);
+    BSORT_LAUNCH("many_merge", many_merge_kernel, mgrid, 256, msm, s, m, static_cast<uint32_t>(R), src);
     src ^= 1;
   }
   BSORT_LAUNCH("many_gather", many_gather_kernel, grid, kThreads, 0, s, m, out_off, out_rec, out_perm);
