@@ -159,6 +159,18 @@ struct ElemOps {
   __device__ Elem<K> ld(uint32_t i) const { return t.get(pad16(i)); }
 };
 
+// Single 64-bit values (a packed key and tile position); exchange slots in
+// one plane.
+struct U64Ops {
+  using T = uint64_t;
+  uint64_t* x;
+  __device__ static bool less(uint64_t a, uint64_t b) { return a < b; }
+  __device__ static uint64_t shfl(uint64_t v, uint32_t m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ static uint64_t inf() { return ~0ull; }
+  __device__ void st(uint32_t i, uint64_t v) const { x[pad16(i)] = v; }
+  __device__ uint64_t ld(uint32_t i) const { return x[pad16(i)]; }
+};
+
 template <typename Ops, int M, int E>
 __device__ __forceinline__ void reg_step(typename Ops::T (&r)[E], const Ops& ops) {
   if constexpr (M < E) {
@@ -257,17 +269,77 @@ __device__ void block_sort(const Ops& ops, uint32_t c, Get get, Sink sink) {
   __syncthreads();
 }
 
+// One level of the network (block size 2^LK: the flip step, then the
+// cleaners 2^(LK-2) .. 1) with every step's partner pattern known at compile
+// time, so no step pays for choosing its exchange form.
+template <typename Ops, int E, int LK>
+__device__ __forceinline__ void bitonic_level(typename Ops::T (&r)[E], const Ops& ops) {
+  bitonic_step<Ops, E>(r, ops, (1u << LK) - 1);
+#pragma unroll
+  for (int lj = LK - 2; lj >= 0; --lj) bitonic_step<Ops, E>(r, ops, 1u << lj);
+}
+
+// block_sort with the network's levels unrolled (a level chosen once per
+// block size instead of once per step); c <= 4,096.
+template <typename Ops, int E, typename Get, typename Sink>
+__device__ void block_sort_unrolled(const Ops& ops, uint32_t c, Get get, Sink sink) {
+  using T = typename Ops::T;
+  const uint32_t tid = threadIdx.x;
+  T r[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const uint32_t i = tid * E + j;
+    r[j] = i < c ? get(i) : Ops::inf();
+  }
+  uint32_t N = 2;
+  while (N < c) N <<= 1;
+  if (N < E) N = E;
+  for (uint32_t lk = 1; (1u << lk) <= N; ++lk) {
+    switch (lk) {
+      case 1: bitonic_level<Ops, E, 1>(r, ops); break;
+      case 2: bitonic_level<Ops, E, 2>(r, ops); break;
+      case 3: bitonic_level<Ops, E, 3>(r, ops); break;
+      case 4: bitonic_level<Ops, E, 4>(r, ops); break;
+      case 5: bitonic_level<Ops, E, 5>(r, ops); break;
+      case 6: bitonic_level<Ops, E, 6>(r, ops); break;
+      case 7: bitonic_level<Ops, E, 7>(r, ops); break;
+      case 8: bitonic_level<Ops, E, 8>(r, ops); break;
+      case 9: bitonic_level<Ops, E, 9>(r, ops); break;
+      case 10: bitonic_level<Ops, E, 10>(r, ops); break;
+      case 11: bitonic_level<Ops, E, 11>(r, ops); break;
+      default: bitonic_level<Ops, E, 12>(r, ops); break;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < E; ++j)
+    if (tid * E + j < c) sink(tid * E + j, r[j]);
+  __syncthreads();
+}
+
 // Exchange slots of the register network over T positions (padded by pad16).
 __host__ __device__ constexpr uint32_t tile_xslots(uint32_t T) { return T + T / 16; }
+
+// Words of at most kPackMaxLen bytes leave the low 16 bits of their one key
+// word zero: the tile sort packs the tile position there (T <= 65,536).
+constexpr uint32_t kPackMaxLen = 6;
+
+// Byte offset (from the planes' start) of the packed network's exchange
+// plane: after a one-key tile's key and index planes.
+__host__ __device__ constexpr size_t tile_packed_xoff(uint32_t T) {
+  return ((static_cast<size_t>(T) + 2) * 8 + (static_cast<size_t>(T) + 4) * 4 + 15) / 16 * 16;
+}
 
 // Shared memory of a tile-sort CTA: [mbarrier 16 B][KW key planes of T+2][idx T+4],
 // plus 128 bytes of slack to align the start.  The register network (one or
 // two key words) reuses the same area for its exchange planes once the tile
-// is in registers, so the area is the larger of the two.
+// is in registers; the packed network of a one-key tile keeps the index plane
+// and puts its one exchange plane after it.  The area is the largest of these.
 __host__ __device__ inline size_t tile_smem_bytes(uint32_t KW, uint32_t T) {
   const size_t planes = static_cast<size_t>(KW) * (T + 2) * 8 + static_cast<size_t>(T + 4) * 4;
   const size_t xch = static_cast<size_t>(tile_xslots(T)) * (8 * (KW < 2 ? KW : 2) + 4);
-  return 128 + 16 + (planes > xch ? planes : xch);
+  const size_t packed = tile_packed_xoff(T) + static_cast<size_t>(tile_xslots(T)) * 8;
+  const size_t a = planes > xch ? planes : xch;
+  return 128 + 16 + (a > packed ? a : packed);
 }
 
 __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
@@ -317,6 +389,23 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
   const uint32_t E = T / blockDim.x;
   if (odd_even) {
     odd_even_tile<K>(t, tr.len);
+  } else if (K == 1 && tr.L <= kPackMaxLen && T % blockDim.x == 0 && (E == 2 || E == 4)) {
+    // one 64-bit value per position: the key with the tile position in its
+    // zero low 16 bits (distinct values, ordered as (key, position), and the
+    // position order is the index order inside a bucket); the index comes
+    // back from the untouched index plane
+    const U64Ops ops{reinterpret_cast<uint64_t*>(smem + 16 + tile_packed_xoff(T))};
+    const uint64_t* kp = t.k[0];
+    const uint32_t* ip = t.idx;
+    auto get = [&](uint32_t i) { return kp[i] | i; };
+    auto sink = [&](uint32_t i, uint64_t v) {
+      const uint64_t g = static_cast<uint64_t>(tr.start) + i;
+      ws.keys[0][g] = v & ~0xFFFFull;
+      ws.idx[0][g] = ip[v & 0xFFFFu];
+    };
+    if (E == 2) block_sort_unrolled<U64Ops, 2>(ops, tr.len, get, sink);
+    else block_sort_unrolled<U64Ops, 4>(ops, tr.len, get, sink);
+    return;
   } else if (K <= 2 && T % blockDim.x == 0 && (E == 2 || E == 4 || (E == 8 && K == 1))) {
     // bitonic network over registers, E positions per thread; only the
     // cross-warp steps go through shared memory (one barrier pair each),

@@ -18,7 +18,9 @@
 //   many_tplan_kernel   tiles per segment (prefix sums)
 //   many_tile_kernel    odd-even or bitonic tile sort (TMA-staged), as in
 //                       the single-list path
-//   many_pplan / many_merge_kernel  merge-path passes per segment
+//   many_pplan_kernel   partitions of every merge pass (segments ordered by
+//                       their pass count, one prefix sum)
+//   many_split / many_merge_kernel  merge-path passes per segment
 //   many_gather_kernel  records and permutation (index within the list)
 //   many_finish_kernel  per-list status
 #include "block_scan.cuh"
@@ -40,14 +42,20 @@ struct ListState {
   uint32_t flags;  // bit c: error code c seen for this list
 };
 
+// Passes of a merge sort over at most 2^32 positions from tiles of >= 64.
+constexpr uint32_t kMaxPasses = 32;
+
 struct ManyHdr {
-  uint32_t items, tiles, parts, flags;
+  uint32_t items, tiles, flags;
+  uint32_t active;                 // segments that take at least one merge pass
+  uint32_t pass_parts[kMaxPasses];  // partitions of merge pass p
 };
+static_assert(sizeof(ManyHdr) <= 256, "the header's WsHeader starts at byte 256");
 
 // Workspace of bsort_sort_many, a pure function of (cap, W, n_lists).
 struct ManyLayout {
-  size_t header, lists, item_start, segs, seg_cnt, tile_pre, part_pre, splits, table, keys_a, keys_b,
-      idx_a, idx_b, trec, tlen, total;
+  size_t header, lists, item_start, segs, seg_cnt, tile_pre, part_pre, seg_ord, splits, table, keys_a,
+      keys_b, idx_a, idx_b, trec, tlen, total;
   uint64_t cap, items_max;
 };
 
@@ -72,6 +80,8 @@ constexpr ManyLayout many_layout_cap(uint64_t cap, uint32_t W, uint32_t n_lists)
   o += align_up(4 * (S + 1), 256);
   l.part_pre = o;
   o += align_up(4 * (S + 1), 256);
+  l.seg_ord = o;
+  o += align_up(4 * S, 256);
   // merge-path splits of one pass: two per partition (at least 64 elements
   // each, plus one partial partition per segment)
   l.splits = o;
@@ -115,7 +125,8 @@ struct Many {
   uint32_t* seg_start;
   uint32_t* seg_cnt;
   uint32_t* tile_pre;
-  uint32_t* part_pre;
+  uint32_t* part_pre;  // over seg_ord[0 .. active)
+  uint32_t* seg_ord;   // segments that take merge passes, most passes first
   uint32_t* table;
   uint8_t* trec;
   uint8_t* tlen;
@@ -137,6 +148,7 @@ Many many_view(void* base, size_t ws_bytes, uint32_t W, uint32_t n_lists, const 
   m.seg_cnt = reinterpret_cast<uint32_t*>(b + l.seg_cnt);
   m.tile_pre = reinterpret_cast<uint32_t*>(b + l.tile_pre);
   m.part_pre = reinterpret_cast<uint32_t*>(b + l.part_pre);
+  m.seg_ord = reinterpret_cast<uint32_t*>(b + l.seg_ord);
   m.table = reinterpret_cast<uint32_t*>(b + l.table);
   m.trec = reinterpret_cast<uint8_t*>(b + l.trec);
   m.tlen = reinterpret_cast<uint8_t*>(b + l.tlen);
@@ -247,7 +259,8 @@ __global__ void many_init_kernel(Many m, int text) {
     m.ls[i].flags = flags;
   }
   if (threadIdx.x == 0) {
-    m.hdr->items = m.hdr->tiles = m.hdr->parts = 0;
+    m.hdr->items = m.hdr->tiles = m.hdr->active = 0;
+    for (uint32_t p = 0; p < kMaxPasses; ++p) m.hdr->pass_parts[p] = 0;
     m.hdr->flags = 0;
     m.ws.hdr->status_flags = 0;
   }
@@ -576,28 +589,68 @@ __global__ void __launch_bounds__(1024) many_tile_kernel(Many m, uint32_t cross)
   }
 }
 
-__global__ void __launch_bounds__(1024) many_pplan_kernel(Many m, uint32_t R) {
-  const uint32_t S = m.n_lists * m.W;
-  const uint32_t tot = block_scan_into(
-      S,
-      [&](uint32_t s) {
-        const uint32_t c = m.seg_cnt[s], P = merge_part_for(m.part, keys_for_len(s % m.W + 1));
-        return c > R ? (c + P - 1) / P : 0u;
+// The partitions of every merge pass at once.  A segment of c > T words takes
+// merge_passes(c, T) passes; ordering the segments by that count, most first
+// (seg_ord), makes the segments still merging at pass p a prefix of the
+// order, so one prefix sum of their partition counts (part_pre) serves every
+// pass: pass p has pass_parts[p] partitions, the first ones of the order.
+__global__ void __launch_bounds__(1024) many_pplan_kernel(Many m) {
+  __shared__ uint32_t hist[kMaxPasses + 1], cursor[kMaxPasses + 1];
+  const uint32_t S = m.n_lists * m.W, T = m.T, lane = lane_id();
+  if (threadIdx.x <= kMaxPasses) hist[threadIdx.x] = 0;
+  __syncthreads();
+  const auto passes = [&](uint32_t s) { return s < S ? min(merge_passes(m.seg_cnt[s], T), kMaxPasses) : 0u; };
+  for (uint32_t b = 0; b < S; b += blockDim.x) {
+    const uint32_t c = passes(b + threadIdx.x);
+    const uint32_t peers = __match_any_sync(0xffffffffu, c);
+    if (c != 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[c], __popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t c = kMaxPasses; c >= 1; --c) {
+      cursor[c] = run;
+      run += hist[c];
+    }
+    m.hdr->active = run;
+  }
+  __syncthreads();
+  for (uint32_t b = 0; b < S; b += blockDim.x) {
+    const uint32_t s = b + threadIdx.x, c = passes(s);
+    const uint32_t peers = __match_any_sync(0xffffffffu, c);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (c != 0 && lane == leader) base = atomicAdd(&cursor[c], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (c != 0) m.seg_ord[base + __popc(peers & lanemask_lt())] = s;
+  }
+  __syncthreads();
+  const uint32_t active = m.hdr->active;
+  block_scan_into(
+      active,
+      [&](uint32_t j) {
+        const uint32_t sg = m.seg_ord[j], P = merge_part_for(m.part, keys_for_len(sg % m.W + 1));
+        return (m.seg_cnt[sg] + P - 1) / P;
       },
       m.part_pre);
-  if (threadIdx.x == 0) m.hdr->parts = tot;
+  __syncthreads();
+  if (threadIdx.x < kMaxPasses) {
+    // segments with more than p passes: the first sum(hist[c], c > p)
+    uint32_t k = 0;
+    for (uint32_t c = threadIdx.x + 1; c <= kMaxPasses; ++c) k += hist[c];
+    m.hdr->pass_parts[threadIdx.x] = m.part_pre[k];
+  }
 }
 
 // The split of every partition of one merge pass, one warp per partition.
-__global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t R, int src) {
-  const uint32_t S = m.n_lists * m.W;
-  const uint32_t parts = m.hdr->parts;
+__global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t pass, uint32_t R, int src) {
+  const uint32_t parts = m.hdr->pass_parts[pass], active = m.hdr->active;
   const uint32_t warps = gridDim.x * (blockDim.x / 32);
   for (uint32_t p = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); p < parts; p += warps) {
-    const uint32_t s = upper_index(m.part_pre, S + 1, p);
+    const uint32_t j = upper_index(m.part_pre, active + 1, p), s = m.seg_ord[j];
     const uint32_t L = s % m.W + 1;
     const uint32_t P = merge_part_for(m.part, keys_for_len(L));
-    const uint32_t o0 = (p - m.part_pre[s]) * P;
+    const uint32_t o0 = (p - m.part_pre[j]) * P;
     const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
     uint32_t* out = m.ws.splits + p;
     switch (keys_for_len(L)) {
@@ -612,24 +665,24 @@ __global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t R, int
 // One merge pass over the partitions of every segment longer than R, each
 // persistent CTA's inputs staged by bulk copies one partition ahead
 // (merge_pass_staged).
-__global__ void __launch_bounds__(256) many_merge_kernel(Many m, uint32_t R, int src) {
+__global__ void __launch_bounds__(256) many_merge_kernel(Many m, uint32_t pass, uint32_t R, int src) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const uint32_t S = m.n_lists * m.W;
+  const uint32_t active = m.hdr->active;
   const auto part_of = [&](uint32_t p, uint32_t* K, uint32_t* P, uint32_t* bstart, uint32_t* cnt, uint32_t* o0) {
-    const uint32_t s = upper_index(m.part_pre, S + 1, p);
+    const uint32_t j = upper_index(m.part_pre, active + 1, p), s = m.seg_ord[j];
     *K = keys_for_len(s % m.W + 1);
     *P = merge_part_for(m.part, *K);
-    *o0 = (p - m.part_pre[s]) * *P;
+    *o0 = (p - m.part_pre[j]) * *P;
     *bstart = m.seg_start[s];
     *cnt = m.seg_cnt[s];
   };
-  merge_pass_staged(align128(smem), m.part, m.hdr->parts, R, src, m.ws, part_of);
+  merge_pass_staged(align128(smem), m.part, m.hdr->pass_parts[pass], R, src, m.ws, part_of);
 }
 
 __global__ void __launch_bounds__(kThreads)
 many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __restrict__ out_rec,
                    uint32_t* __restrict__ out_perm) {
-  __shared__ uint32_t s_off[kMaxW + 2];
+  __shared__ uint32_t s_off[kMaxW + 2], s_buf[kMaxW + 2];
   const uint32_t W = m.W, KW = W / 8, T = m.T;
   const uint32_t items = m.hdr->items;
   const Ws& ws = m.ws;
@@ -637,6 +690,10 @@ many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __rest
     const uint32_t i = upper_index(m.item_start, m.n_lists + 1, it);
     const uint64_t off = m.lists[i].word_off;
     if (threadIdx.x < W + 2) s_off[threadIdx.x] = out_off[static_cast<uint64_t>(i) * (W + 2) + threadIdx.x];
+    __syncthreads();
+    // the buffer each length's sorted segment ends in
+    if (threadIdx.x >= 1 && threadIdx.x <= W)
+      s_buf[threadIdx.x] = merge_passes(s_off[threadIdx.x + 1] - s_off[threadIdx.x], T) & 1u;
     __syncthreads();
     const uint32_t n = s_off[W + 1];
     const uint32_t j0 = (it - m.item_start[i]) * kItemWords, j1 = min(n, j0 + kItemWords);
@@ -652,7 +709,7 @@ many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __rest
         L = lo;
       }
       const uint32_t K = keys_for_len(L);
-      const int buf = static_cast<int>(merge_passes(s_off[L + 1] - s_off[L], T) & 1u);
+      const int buf = static_cast<int>(s_buf[L]);
       const uint64_t g = off + r;
       const uint64_t* kb = buf ? ws.keys[1] : ws.keys[0];
       const uint32_t* ib = buf ? ws.idx[1] : ws.idx[0];
@@ -722,10 +779,11 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "many_tile_odd_even" : "many_tile_bitonic", many_tile_kernel,
                grid, p.threads, tsm, s, m, p.cross);
   int src = 0;
-  for (uint64_t R = p.tile; R < max_list_words; R <<= 1) {
-    BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m, static_cast<uint32_t>(R));
-    BSORT_LAUNCH("many_split", many_split_kernel, grid * 2, 256, 0, s, m, static_cast<uint32_t>(R), src);
-    BSORT_LAUNCH("many_merge", many_merge_kernel, mgrid, 256, msm, s, m, static_cast<uint32_t>(R), src);
+  if (p.tile < max_list_words) BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m);
+  uint32_t pass = 0;
+  for (uint64_t R = p.tile; R < max_list_words && pass < kMaxPasses; R <<= 1, ++pass) {
+    BSORT_LAUNCH("many_split", many_split_kernel, grid * 2, 256, 0, s, m, pass, static_cast<uint32_t>(R), src);
+    BSORT_LAUNCH("many_merge", many_merge_kernel, mgrid, 256, msm, s, m, pass, static_cast<uint32_t>(R), src);
     src ^= 1;
   }
   BSORT_LAUNCH("many_gather", many_gather_kernel, grid, kThreads, 0, s, m, out_off, out_rec, out_perm);
