@@ -36,4 +36,57 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
   return r;
 }
 
+
+// Exclusive scan of f(0..n-1) by one block of 1,024 threads into
+// out[0..n-1], the total to *total_at (when given) and returned.  out may be
+// the array f reads: each chunk is read whole before it is written.
+template <typename F>
+__device__ uint32_t block_scan_into(uint32_t n, F f, uint32_t* out, uint32_t* total_at) {
+  // chunks of kScanChunk values: read with coalesced accesses (all of a
+  // thread's reads in flight together) into shared memory, scanned there,
+  // written back coalesced; a running carry joins the chunks
+  constexpr uint32_t kScanChunk = 8192;
+  constexpr uint32_t kPer = kScanChunk / 1024;
+  __shared__ uint32_t tmp[1024 / 32 + 1];
+  __shared__ uint32_t chunk[kScanChunk];
+  uint32_t carry = 0;
+  for (uint32_t c0 = 0; c0 < n; c0 += kScanChunk) {
+    const uint32_t m = min(kScanChunk, n - c0);
+    uint32_t vals[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = k * blockDim.x + threadIdx.x;
+      vals[k] = i < m ? f(c0 + i) : 0u;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = k * blockDim.x + threadIdx.x;
+      if (i < kScanChunk) chunk[i] = vals[k];
+    }
+    __syncthreads();
+    // thread t scans positions t kPer .. t kPer + kPer - 1 of the chunk
+    uint32_t mine[kPer], s = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x * kPer + k;
+      mine[k] = i < kScanChunk ? chunk[i] : 0u;
+      s += mine[k];
+    }
+    uint32_t tot;
+    uint32_t run = carry + block_exclusive_scan(s, tmp, &tot);
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x * kPer + k;
+      if (i < kScanChunk) chunk[i] = run;
+      run += mine[k];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) out[c0 + i] = chunk[i];
+    carry += tot;
+    __syncthreads();  // the chunk is reused
+  }
+  if (threadIdx.x == 0 && total_at) *total_at = carry;
+  return carry;
+}
+
 }  // namespace bsort

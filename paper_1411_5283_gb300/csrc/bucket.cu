@@ -5,7 +5,8 @@
 //   hist_kernel     per-block length histogram: each warp aggregates equal
 //                   lengths with __match_any_sync, one shared-memory counter
 //                   row per warp, then a block reduction -> table[L][b]
-//   scan_kernel     exclusive scan of the L-major table: base[L][b] is the
+//   scan_kernel     exclusive scan of the L-major table (chunks read and
+//                   written coalesced through shared memory): base[L][b] is the
 //                   first output slot of block b's words of length L
 //   off_kernel      bucket offsets off[L] = base[L][0], off[W+1] = n
 //   scatter_kernel  stable scatter: word i goes to base[L][b] + (number of
@@ -127,21 +128,8 @@ scatter_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
 }
 
 __global__ void __launch_bounds__(1024)
-scan_kernel(uint32_t* __restrict__ data, uint32_t n, uint32_t* __restrict__ total) {
-  __shared__ uint32_t tmp[1024 / 32 + 1];
-  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-  const uint32_t b = threadIdx.x * per;
-  const uint32_t e = min(n, b + per);
-  uint32_t s = 0;
-  for (uint32_t i = b; i < e; ++i) s += data[i];
-  uint32_t tot;
-  uint32_t run = block_exclusive_scan(s, tmp, &tot);
-  for (uint32_t i = b; i < e; ++i) {
-    const uint32_t v = data[i];
-    data[i] = run;
-    run += v;
-  }
-  if (threadIdx.x == 0) *total = tot;
+scan_kernel(uint32_t* data, uint32_t n, uint32_t* __restrict__ total) {
+  block_scan_into(n, [&](uint32_t i) { return data[i]; }, data, total);
 }
 
 }  // namespace

@@ -118,10 +118,11 @@ constexpr WsLayout ws_layout_cap(uint64_t cap, uint32_t W) {
   o += align_up(4 * third, 256);
   l.misc = o;
   o += 64 * 1024;
-  // merge-path splits of one merge pass: two per partition, partitions of at
-  // least 64 elements (the smallest partition of the widest words)
+  // merge-path splits of one merge pass: one per partition, partitions of at
+  // least 64 elements (the smallest partition of the widest words) plus a
+  // partial one per bucket
   l.splits = o;
-  o += align_up(4 * 2 * (cap / 64 + 2 * static_cast<size_t>(kBins)), 256);
+  o += align_up(4 * (cap / 64 + 2 * static_cast<size_t>(kBins) + 1), 256);
   l.autoa = o;
   o += auto_bytes(cap, W);
   l.total = o;
@@ -165,7 +166,7 @@ struct Ws {
   uint32_t* table;
   uint8_t* autoa;     // sample-sort area (samples, splitters, segment tables)
   uint32_t* misc;     // 64 KB of small per-call state (e.g. internal bucket offsets)
-  uint32_t* splits;   // merge-path splits of the current merge pass
+  uint32_t* splits;   // merge-path splits of the current merge pass, one per partition
   uint64_t* keys[2];
   uint32_t* idx[2];
   uint64_t cap;
@@ -342,6 +343,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {

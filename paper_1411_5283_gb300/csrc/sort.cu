@@ -10,8 +10,12 @@
 //                      form: alternate even / odd neighbour exchanges, stop
 //                      after an even and an odd phase without exchange) or by
 //                      a bitonic network;
+//   merge_split_kernel the merge-path splits of a pass over long runs, one
+//                      warp per partition, all at once;
 //   merge_pass_kernel  merge-path merging of neighbouring sorted runs, run
-//                      length doubling each pass, until each bucket is one run.
+//                      length doubling each pass, until each bucket is one run
+//                      (a producer warp per CTA finds or reads the splits and
+//                      stages the inputs by bulk copies, consumer warps merge).
 // Elements are (key words..., input index); comparing the tuple is a strict
 // total order, so every algorithm and tile size gives the same result.
 #include <algorithm>
@@ -87,9 +91,8 @@ __device__ void pass_partitions(const uint32_t* s_off, uint32_t W, uint32_t R, u
   }
 }
 
-// The split of every partition of one merge pass, one warp per partition
-// (all partitions' searches at once, instead of each merge CTA waiting for
-// its own): splits[q] for partition q.
+// The split of every partition of one merge pass, one warp per partition,
+// all at once: splits[q] at partition q's first output.
 __global__ void __launch_bounds__(256)
 merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, uint32_t part, int src,
                    Ws ws) {
@@ -117,11 +120,13 @@ merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, u
 
 // One merge pass over every bucket longer than R: output ranges of each
 // bucket cut into partitions (merge_part_for(part, K) elements, so that one
-// shared-memory size fits every key count), handed to persistent CTAs by a
-// grid-stride loop over the partitions of all buckets, each CTA's inputs
-// staged by bulk copies one partition ahead (merge_pass_staged).
-__global__ void __launch_bounds__(256) merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W,
-                                                           uint32_t R, uint32_t part, int src, Ws ws) {
+// shared-memory size fits every key count), numbered over all buckets and
+// handed to persistent CTAs in contiguous chunks (merge_pass_ws: a producer
+// warp finds the splits and stages the inputs by bulk copies, the consumer
+// warps merge).
+__global__ void __launch_bounds__(kMergeThreads) merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W,
+                                                                   uint32_t R, uint32_t part, int src, Ws ws,
+                                                                   int presplit) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2], s_pre[kMaxW + 2];
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(256) merge_pass_kernel(const uint32_t* __restr
   pass_partitions(s_off, W, R, part, s_pre);
   __syncthreads();
   const uint32_t total = s_pre[W + 1];
-  // thread 0 walks its partitions in increasing order, so the length search
+  // a thread walks its partitions in increasing order, so the length search
   // only moves forward
   uint32_t L = 1;
   const auto part_of = [&](uint32_t q, uint32_t* K, uint32_t* P, uint32_t* bstart, uint32_t* cnt, uint32_t* o0) {
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(256) merge_pass_kernel(const uint32_t* __restr
     *bstart = s_off[L];
     *cnt = s_off[L + 1] - s_off[L];
   };
-  merge_pass_staged(align128(smem), part, total, R, src, ws, part_of);
+  merge_pass_ws(align128(smem), part, total, R, src, ws, presplit ? ws.splits : nullptr, part_of);
 }
 
 }  // namespace
@@ -159,9 +164,9 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   const uint32_t tiles = (n_cap + T - 1) / T + W;
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "tile_odd_even" : "tile_bitonic", tile_sort_kernel, tiles,
                p.threads, tsm, s, d_off, W, T, p.cross, ws);
-  // persistent merge CTAs: as many as fit the SMs (shared memory, 256 threads)
+  // persistent merge CTAs: as many as fit the SMs
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, merge_pass_kernel, 256, msm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, merge_pass_kernel, kMergeThreads, msm);
   if (e != cudaSuccess) return e;
   const uint32_t per_sm = occ < 1 ? 1u : occ > 8 ? 8u : static_cast<uint32_t>(occ);
   const uint32_t need = (n_cap + part - 1) / part * 4 + W;  // partitions are at most part / 4
@@ -171,10 +176,12 @@ cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const u
   const uint32_t split_ctas = (need + 7) / 8 < static_cast<uint32_t>(device_sm_count()) * 8
                                   ? (need + 7) / 8 : static_cast<uint32_t>(device_sm_count()) * 8;
   for (uint64_t R = T; R < n_cap; R <<= 1) {
-    BSORT_LAUNCH("merge_split", merge_split_kernel, split_ctas, 256, 0, s, d_off, W,
-                 static_cast<uint32_t>(R), part, src, ws);
-    BSORT_LAUNCH("merge_pass", merge_pass_kernel, parts, 256, msm, s, d_off, W,
-                 static_cast<uint32_t>(R), part, src, ws);
+    const int presplit = n_cap >= kPresplitMinWords && R >= kPresplitMinRun;
+    if (presplit)
+      BSORT_LAUNCH("merge_split", merge_split_kernel, split_ctas, 256, 0, s, d_off, W, static_cast<uint32_t>(R),
+                   part, src, ws);
+    BSORT_LAUNCH("merge_pass", merge_pass_kernel, parts, kMergeThreads, msm, s, d_off, W,
+                 static_cast<uint32_t>(R), part, src, ws, presplit);
     src ^= 1;
   }
   return cudaGetLastError();

@@ -321,7 +321,32 @@ __host__ __device__ constexpr uint32_t tile_xslots(uint32_t T) { return T + T / 
 
 // Words of at most kPackMaxLen bytes leave the low 16 bits of their one key
 // word zero: the tile sort packs the tile position there (T <= 65,536).
+// Letter-only words of up to 8 bytes do the same with 6-bit letter codes.
 constexpr uint32_t kPackMaxLen = 6;
+
+// A one-key word of L <= 8 bytes (big-endian in w) made only of ASCII
+// letters?
+__device__ __forceinline__ bool all_letters(uint64_t w, uint32_t L) {
+  bool ok = true;
+  for (uint32_t i = 0; i < L; ++i) {
+    const uint32_t b = static_cast<uint32_t>(w >> (56 - 8 * i)) & 0xFFu;
+    ok &= ((b | 0x20u) - 0x61u) < 26u;
+  }
+  return ok;
+}
+
+// Its letters as 6-bit codes in byte order (A..Z -> 0..25, a..z -> 26..51,
+// the order of the bytes themselves), first letter highest, the codes ending
+// at bit 16: equal-length letter words compare as their codes do, and the
+// low 16 bits are free.
+__device__ __forceinline__ uint64_t letter_code(uint64_t w, uint32_t L) {
+  uint64_t v = 0;
+  for (uint32_t i = 0; i < L; ++i) {
+    const uint32_t b = static_cast<uint32_t>(w >> (56 - 8 * i)) & 0xFFu;
+    v = (v << 6) | (b >= 0x61u ? b - 0x61u + 26u : b - 0x41u);
+  }
+  return v << (64 - 6 * L);
+}
 
 // Byte offset (from the planes' start) of the packed network's exchange
 // plane: after a one-key tile's key and index planes.
@@ -387,21 +412,37 @@ __device__ void sort_one_tile(uint8_t* smem, uint32_t T, const TileRef& tr, bool
   for (int j = 0; j < K; ++j) t.k[j] = kplane + j * (T + 2) + (tr.start - ks);
   t.idx = iplane + (tr.start - is);
   const uint32_t E = T / blockDim.x;
+  // one-key words sorted as single 64-bit values (see below): words of at
+  // most kPackMaxLen bytes always, those of 7 or 8 bytes when every word of
+  // the tile is letters only (block-uniform test)
+  bool packed = false, coded = false;
+  if (K == 1 && !odd_even && T % blockDim.x == 0 && (E == 2 || E == 4)) {
+    if (tr.L <= kPackMaxLen) {
+      packed = true;
+    } else {
+      bool ok = true;
+      for (uint32_t i = threadIdx.x; i < tr.len; i += blockDim.x) ok &= all_letters(t.k[0][i], tr.L);
+      coded = packed = __syncthreads_and(ok) != 0;
+    }
+  }
   if (odd_even) {
     odd_even_tile<K>(t, tr.len);
-  } else if (K == 1 && tr.L <= kPackMaxLen && T % blockDim.x == 0 && (E == 2 || E == 4)) {
-    // one 64-bit value per position: the key with the tile position in its
-    // zero low 16 bits (distinct values, ordered as (key, position), and the
-    // position order is the index order inside a bucket); the index comes
-    // back from the untouched index plane
+  } else if (packed) {
+    // one 64-bit value per position: the key (or its 6-bit letter codes) with
+    // the tile position in the zero low 16 bits: distinct values, ordered as
+    // (key, position), and the position order is the index order inside a
+    // bucket.  Key and index come back through the position from the
+    // untouched key and index planes.
     const U64Ops ops{reinterpret_cast<uint64_t*>(smem + 16 + tile_packed_xoff(T))};
     const uint64_t* kp = t.k[0];
     const uint32_t* ip = t.idx;
-    auto get = [&](uint32_t i) { return kp[i] | i; };
+    const uint32_t L = tr.L;
+    auto get = [&](uint32_t i) { return (coded ? letter_code(kp[i], L) : kp[i]) | i; };
     auto sink = [&](uint32_t i, uint64_t v) {
       const uint64_t g = static_cast<uint64_t>(tr.start) + i;
-      ws.keys[0][g] = v & ~0xFFFFull;
-      ws.idx[0][g] = ip[v & 0xFFFFu];
+      const uint32_t pos = static_cast<uint32_t>(v & 0xFFFFu);
+      ws.keys[0][g] = kp[pos];
+      ws.idx[0][g] = ip[pos];
     };
     if (E == 2) block_sort_unrolled<U64Ops, 2>(ops, tr.len, get, sink);
     else block_sort_unrolled<U64Ops, 4>(ops, tr.len, get, sink);
@@ -564,34 +605,23 @@ __device__ __forceinline__ SmemTile<K> ws_planes(const Ws& ws, int buf, uint64_t
   return t;
 }
 
-// The split of partition [o0, o0 + part) of a bucket's merge pass: how many
-// of its first o0 - ps outputs come from the first run of its pair (ps the
-// pair's start), found by one warp.  The partition's end split is the next
-// partition's split, or the whole first run at the pair's end.
-template <int K>
-__device__ void merge_split_warp(uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o0, int src,
-                                 const Ws& ws, uint32_t* out) {
-  const SmemTile<K> t = ws_planes<K>(ws, src, bstart);
-  const uint32_t ps = o0 / (2 * R) * (2 * R);
-  const uint32_t na = min(R, cnt - ps), nb = min(R, cnt - ps - na);
-  auto gA = [&](uint32_t i) { return t.get(ps + i); };
-  auto gB = [&](uint32_t i) { return t.get(ps + na + i); };
-  const uint32_t s0 = o0 == ps ? 0u : merge_path_warp<K>(gA, na, gB, nb, o0 - ps);
-  if ((threadIdx.x & 31u) == 0) *out = s0;
-}
-
 // ---------------------------------------------------------------------------
-// Merge pass with bulk-copy staging, two input buffers per CTA
+// Merge pass: a producer warp, consumer warps, two staged input buffers
 // ---------------------------------------------------------------------------
-// A persistent CTA takes partitions q, q + G, q + 2G, ... of one merge pass.
-// While it merges partition q from one shared-memory buffer, the bulk-copy
-// (TMA) engine already fills the other with partition q + G's two input ranges
-// (one copy per key plane and index plane of each run), their splits coming
-// from merge_split_kernel.  The merged partition goes to a third buffer and
-// from there to global memory in coalesced stores.
+// A persistent CTA takes a contiguous chunk of one merge pass's partitions.
+// Its last warp (the producer) finds each partition's split (merge path, 32
+// candidates a round over global memory; consecutive partitions of a run
+// pair share a boundary, so one search per partition), or reads it when a
+// separate launch found them all at once (long runs, whose searches take
+// more rounds than one warp can hide behind the merges), and stages the
+// partition's two input ranges into one of two shared-memory buffers with
+// bulk copies (TMA), one per key plane and index plane of each run.  The other
+// warps (the consumers) merge a staged partition into a third buffer, release
+// its input buffer and write the result out in coalesced stores, while the
+// producer already searches and stages the next ones.
 //
 // Input buffer layout for elements of K key words and partitions of P
-// elements: [mbarrier 16 B][K key planes of P + 32 slots][index plane of
+// elements: [full mbarrier 16 B][K key planes of P + 32 slots][index plane of
 // P + 32 slots].  In each plane the first run's range starts at the plane's
 // start and the second's at the next 16-byte boundary after it; a range is
 // copied from the 16-byte boundary at or below its first element (up to 1 key
@@ -615,20 +645,49 @@ __host__ __device__ constexpr size_t merge_out_bytes(uint32_t part) {
   return (static_cast<size_t>(part) * 12 + 127) / 128 * 128;
 }
 
-// Shared memory of a staged merge CTA.
+// Shared memory of a merge CTA (without the 128 bytes of alignment slack).
 __host__ __device__ constexpr size_t merge_staged_smem_bytes(uint32_t part) {
   return 2 * merge_buf_bytes(part) + merge_out_bytes(part);
 }
 
+// On tables of at least kPresplitMinWords words, merge passes over runs of at
+// least kPresplitMinRun find their splits in a separate launch (all
+// partitions at once): those searches run over data in HBM and take more
+// rounds than one producer warp hides behind the merges.  Shorter runs, and
+// smaller tables (mostly in L2), search in the merge kernel.
+constexpr uint64_t kPresplitMinRun = 4096;
+constexpr uint64_t kPresplitMinWords = 1u << 20;
+
+// Consumer threads of a merge CTA; the CTA has one more warp, the producer.
+constexpr uint32_t kMergeConsumers = 256;
+constexpr uint32_t kMergeThreads = kMergeConsumers + 32;
+
 __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
 
-// Thread 0: the geometry of partition [o0, o0 + P) of a pass over runs of R
-// of a bucket (cnt elements at bstart of buffer src) whose raw splits are s0
-// and s1; issues the partition's bulk copies into buf, whose barrier is told
-// the bytes to expect.
-__device__ inline MergeGeo merge_issue(uint8_t* buf, uint32_t K, uint32_t P, uint32_t bstart, uint32_t cnt,
-                                       uint32_t o0, uint32_t R, int src, const Ws& ws, uint32_t s0,
-                                       uint32_t s1) {
+// Barrier of the consumer warps only (named barrier 1).
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kMergeConsumers) : "memory");
+}
+
+// AND of p over the consumer warps (named barrier 1).
+__device__ __forceinline__ bool consumers_and(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.and.pred b, 1, %2, a;\n"
+      " selp.u32 %0, 1, 0, b;\n}\n"
+      : "=r"(r)
+      : "r"(p ? 1u : 0u), "r"(kMergeConsumers)
+      : "memory");
+  return r != 0;
+}
+
+// Producer lane 0: the geometry of partition [o0, o0 + P) of a pass over runs
+// of R of a bucket (cnt elements at bstart of buffer src) whose raw splits are
+// s0 and s1, written to *gp; then the bytes to expect on buf's barrier and the
+// partition's bulk copies into buf.
+__device__ inline void merge_issue(uint8_t* buf, MergeGeo* gp, uint32_t K, uint32_t P, uint32_t bstart,
+                                   uint32_t cnt, uint32_t o0, uint32_t R, int src, const Ws& ws, uint32_t s0,
+                                   uint32_t s1) {
   MergeGeo g;
   g.K = K;
   g.P = P;
@@ -659,6 +718,7 @@ __device__ inline MergeGeo merge_issue(uint8_t* buf, uint32_t K, uint32_t P, uin
   const uint32_t ibA = g.ca ? round16((g.aAi + g.ca) * 4) : 0u, ibB = g.cb ? round16((g.aBi + g.cb) * 4) : 0u;
   g.bB = kbA;
   g.bBi = ibA;
+  *gp = g;  // published to the consumers by the barrier's release below
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf);
   const uint32_t ks = (P + 32) * 8;
   uint8_t* ib = buf + 16 + K * ks;
@@ -672,13 +732,47 @@ __device__ inline MergeGeo merge_issue(uint8_t* buf, uint32_t K, uint32_t P, uin
   }
   if (ibA) bulk_g2s(ib, ws.idx[src] + (gA - g.aAi), ibA, bar);
   if (ibB) bulk_g2s(ib + ibA, ws.idx[src] + (gB - g.aBi), ibB, bar);
-  return g;
 }
 
-// Merges a staged partition into `out` (thread t produces outputs
-// [t per, t per + per)), then writes it to buffer src ^ 1 in coalesced stores.
+// Producer warp: the split at output o of a bucket's pass (cnt elements at
+// bstart of buffer src): how many of the first o - ps outputs of o's run pair
+// come from its first run.  Every lane returns it.
 template <int K>
-__device__ void merge_staged(const uint8_t* buf, uint8_t* out, const MergeGeo& g, int src, const Ws& ws) {
+__device__ uint32_t merge_split_at(uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o, int src, const Ws& ws) {
+  const SmemTile<K> t = ws_planes<K>(ws, src, bstart);
+  const uint32_t ps = o / (2 * R) * (2 * R);
+  const uint32_t na = min(R, cnt - ps), nb = min(R, cnt - ps - na);
+  auto gA = [&](uint32_t i) { return t.get(ps + i); };
+  auto gB = [&](uint32_t i) { return t.get(ps + na + i); };
+  return merge_path_warp<K>(gA, na, gB, nb, o - ps);
+}
+
+// One warp: the split at partition q's first output o0 into out (0 at a run
+// pair's start), for merge_pass_ws's precomputed form.
+template <int K>
+__device__ void merge_split_warp(uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o0, int src, const Ws& ws,
+                                 uint32_t* out) {
+  const uint32_t ps = o0 / (2 * R) * (2 * R);
+  const uint32_t s0 = o0 == ps ? 0u : merge_split_at<K>(bstart, cnt, R, o0, src, ws);
+  if ((threadIdx.x & 31u) == 0) *out = s0;
+}
+
+__device__ __forceinline__ uint32_t merge_split_any(uint32_t K, uint32_t bstart, uint32_t cnt, uint32_t R, uint32_t o,
+                                                    int src, const Ws& ws) {
+  switch (K) {
+    case 1: return merge_split_at<1>(bstart, cnt, R, o, src, ws);
+    case 2: return merge_split_at<2>(bstart, cnt, R, o, src, ws);
+    case 3: return merge_split_at<3>(bstart, cnt, R, o, src, ws);
+    default: return merge_split_at<4>(bstart, cnt, R, o, src, ws);
+  }
+}
+
+// Consumers: merge a staged partition into `out` (thread t produces outputs
+// [t per, t per + per)), release the input buffer (rel), write the result to
+// buffer src ^ 1 in coalesced stores.
+template <int K>
+__device__ void merge_staged(const uint8_t* buf, uint8_t* out, const MergeGeo& g, int src, const Ws& ws,
+                             uint64_t* rel) {
   const uint32_t ks = (g.P + 32) * 8;
   const uint8_t* ibase = buf + 16 + K * ks;
   const auto A = [&](uint32_t i) {
@@ -700,7 +794,7 @@ __device__ void merge_staged(const uint8_t* buf, uint8_t* out, const MergeGeo& g
   for (int k = 0; k < K; ++k) o.k[k] = reinterpret_cast<uint64_t*>(out) + k * g.P;
   o.idx = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(out) + K * g.P);
   const uint32_t tot = g.ca + g.cb;
-  const uint32_t per = (g.P + blockDim.x - 1) / blockDim.x;
+  const uint32_t per = (g.P + kMergeConsumers - 1) / kMergeConsumers;
   const uint32_t d0 = min(tot, threadIdx.x * per), d1 = min(tot, d0 + per);
   uint32_t ia = merge_path<K>(A, g.ca, B, g.cb, d0), ib = d0 - ia;
   // the two heads stay in registers; only the side taken is read again
@@ -714,65 +808,110 @@ __device__ void merge_staged(const uint8_t* buf, uint8_t* out, const MergeGeo& g
       if (++ib < g.cb) b = B(ib);
     }
   }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < tot; i += blockDim.x) store_elem<K>(ws, src ^ 1, g.out0 + i, o.get(i));
+  consumers_sync();
+  if (threadIdx.x == 0) mbar_arrive(rel);  // the input buffer is free for the producer
+  for (uint32_t i = threadIdx.x; i < tot; i += kMergeConsumers) store_elem<K>(ws, src ^ 1, g.out0 + i, o.get(i));
 }
 
-// One merge pass over `total` partitions; part_of(q, &K, &P, &bstart, &cnt,
-// &o0) describes partition q, whose split (merge_split_warp) is ws.splits[q].
-// Partitions of one bucket are numbered consecutively, so partition q's end
-// split is ws.splits[q + 1] unless q ends its run pair.
-// smem (128-byte aligned) holds merge_staged_smem_bytes(part).  Returns false
-// (with the status set) when a wait gave up; the copies in flight have then
-// landed (or their wait gave up too).
+// One merge pass over `total` partitions with kMergeThreads threads per CTA;
+// part_of(q, &K, &P, &bstart, &cnt, &o0) describes partition q (partitions of
+// one bucket numbered consecutively, in output order).  With `pre`, the
+// splits were found beforehand (pre[q] at partition q's first output, by
+// merge_split_warp, all partitions at once), else the producer searches.
+// smem (128-byte aligned) holds merge_staged_smem_bytes(part).  A wait that
+// gives up sets BSORT_E_TIMEOUT and makes the CTA stop once the copies in
+// flight landed.
 template <typename PartOf>
-__device__ bool merge_pass_staged(uint8_t* smem, uint32_t part, uint32_t total, uint32_t R, int src,
-                                  const Ws& ws, PartOf part_of) {
+__device__ void merge_pass_ws(uint8_t* smem, uint32_t part, uint32_t total, uint32_t R, int src,
+                              const Ws& ws, const uint32_t* pre, PartOf part_of) {
   __shared__ MergeGeo s_geo[2];
+  __shared__ __align__(8) uint64_t s_empty[2];
+  __shared__ volatile uint32_t s_abort;
   uint8_t* buf[2] = {smem, smem + merge_buf_bytes(part)};
   uint8_t* out = smem + 2 * merge_buf_bytes(part);
   if (threadIdx.x == 0) {
     mbar_init(reinterpret_cast<uint64_t*>(buf[0]), 1);
     mbar_init(reinterpret_cast<uint64_t*>(buf[1]), 1);
+    mbar_init(&s_empty[0], 1);
+    mbar_init(&s_empty[1], 1);
+    s_abort = 0;
     fence_barrier_init();
   }
   __syncthreads();
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};  // thread 0: a copy is in flight into buffer x
-  const auto issue = [&](uint32_t q, int x) {
-    uint32_t K, P, bstart, cnt, o0;
-    part_of(q, &K, &P, &bstart, &cnt, &o0);
-    const uint32_t o1 = min(o0 + P, cnt), ps = o0 / (2 * R) * (2 * R);
-    const uint32_t s1 = o1 - ps == min(2 * R, cnt - ps) ? min(R, cnt - ps) : ws.splits[q + 1];
-    s_geo[x] = merge_issue(buf[x], K, P, bstart, cnt, o0, R, src, ws, ws.splits[q], s1);
-    pending[x] = true;
-  };
-  int b = 0;
-  if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x, 0);
-  for (uint32_t q = blockIdx.x; q < total; q += gridDim.x, b ^= 1) {
-    const uint32_t qn = q + gridDim.x;
-    if (threadIdx.x == 0 && qn < total) issue(qn, b ^ 1);  // buffer b ^ 1 was released last round
-    const bool ok = mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf[b]), phase[b], ws.wait_polls);
-    if (!__syncthreads_and(ok)) {
+  // this CTA's partitions: a contiguous chunk when the producer searches
+  // (neighbours share a split), else q = blockIdx.x + k gridDim.x (CTAs working
+  // on neighbouring partitions at the same time)
+  const uint32_t q0 = static_cast<uint32_t>(static_cast<uint64_t>(total) * blockIdx.x / gridDim.x);
+  const uint32_t q1 = static_cast<uint32_t>(static_cast<uint64_t>(total) * (blockIdx.x + 1) / gridDim.x);
+  const uint32_t count = pre ? (blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u) : q1 - q0;
+  const auto part_at = [&](uint32_t it) { return pre ? blockIdx.x + it * gridDim.x : q0 + it; };
+  if (threadIdx.x >= kMergeConsumers) {
+    // the producer warp
+    const bool lead = (threadIdx.x & 31u) == 0;
+    uint32_t carry = 0;  // split at the previous partition's end
+    bool issued[2] = {false, false};
+    uint32_t last_par[2] = {0u, 0u};  // parity of the last phase issued into each buffer
+    for (uint32_t it = 0; it < count; ++it) {
+      const uint32_t q = part_at(it);
+      const int b = static_cast<int>(it & 1u);
+      if (__any_sync(0xffffffffu, s_abort != 0)) break;
+      if (it >= 2) {  // wait until the consumers released buffer b
+        const uint32_t par = ((it >> 1) - 1) & 1u;
+        bool ok = false;
+        for (uint32_t poll = 0; poll < ws.wait_polls && !ok && !s_abort; ++poll) ok = mbar_try_wait(&s_empty[b], par);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lead) {
+            set_error(ws.hdr, BSORT_E_TIMEOUT);
+            s_abort = 1;
+          }
+          break;
+        }
+      }
+      uint32_t K, P, bstart, cnt, o0;
+      part_of(q, &K, &P, &bstart, &cnt, &o0);
+      const uint32_t o1 = min(o0 + P, cnt), ps = o0 / (2 * R) * (2 * R);
+      const uint32_t pair = min(2 * R, cnt - ps);
+      uint32_t s0 = 0;
+      if (o0 != ps) s0 = pre ? pre[q] : q == q0 ? merge_split_any(K, bstart, cnt, R, o0, src, ws) : carry;
+      const uint32_t s1 = o1 - ps == pair ? min(R, cnt - ps)  // the pair's end: the whole first run
+                          : pre           ? pre[q + 1]
+                                          : merge_split_any(K, bstart, cnt, R, o1, src, ws);
+      carry = s1;
+      if (lead) merge_issue(buf[b], &s_geo[b], K, P, bstart, cnt, o0, R, src, ws, s0, s1);
+      issued[b] = true;
+      last_par[b] = (it >> 1) & 1u;
+      __syncwarp();
+    }
+    if (lead && s_abort) {
+      // let this CTA's copies in flight land before it exits
+      for (int x = 0; x < 2; ++x)
+        if (issued[x]) mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf[x]), last_par[x]);
+    }
+    return;
+  }
+  // the consumer warps
+  for (uint32_t it = 0; it < count; ++it) {
+    const int b = static_cast<int>(it & 1u);
+    const uint32_t par = (it >> 1) & 1u;
+    bool ok = false;
+    for (uint32_t poll = 0; poll < ws.wait_polls && !ok && !s_abort; ++poll)
+      ok = mbar_try_wait(reinterpret_cast<uint64_t*>(buf[b]), par);
+    if (!consumers_and(ok)) {
       if (threadIdx.x == 0) {
         set_error(ws.hdr, BSORT_E_TIMEOUT);
-        for (int x = 0; x < 2; ++x)  // let the copies in flight land before the CTA exits
-          if (pending[x]) mbar_wait_bounded(reinterpret_cast<uint64_t*>(buf[x]), phase[x]);
+        s_abort = 1;
       }
-      return false;
+      return;
     }
-    phase[b] ^= 1u;
-    pending[b] = false;
     const MergeGeo g = s_geo[b];
     switch (g.K) {
-      case 1: merge_staged<1>(buf[b], out, g, src, ws); break;
-      case 2: merge_staged<2>(buf[b], out, g, src, ws); break;
-      case 3: merge_staged<3>(buf[b], out, g, src, ws); break;
-      default: merge_staged<4>(buf[b], out, g, src, ws); break;
+      case 1: merge_staged<1>(buf[b], out, g, src, ws, &s_empty[b]); break;
+      case 2: merge_staged<2>(buf[b], out, g, src, ws, &s_empty[b]); break;
+      case 3: merge_staged<3>(buf[b], out, g, src, ws, &s_empty[b]); break;
+      default: merge_staged<4>(buf[b], out, g, src, ws, &s_empty[b]); break;
     }
-    __syncthreads();  // buffer b, its geometry and the output buffer are free again
+    consumers_sync();  // the output buffer is free again
   }
-  return true;
 }
 
 }  // namespace bsort

@@ -20,7 +20,7 @@
 //                       the single-list path
 //   many_pplan_kernel   partitions of every merge pass (segments ordered by
 //                       their pass count, one prefix sum)
-//   many_split / many_merge_kernel  merge-path passes per segment
+//   many_merge_kernel   merge-path passes per segment
 //   many_gather_kernel  records and permutation (index within the list)
 //   many_finish_kernel  per-list status
 #include "block_scan.cuh"
@@ -54,7 +54,7 @@ static_assert(sizeof(ManyHdr) <= 256, "the header's WsHeader starts at byte 256"
 
 // Workspace of bsort_sort_many, a pure function of (cap, W, n_lists).
 struct ManyLayout {
-  size_t header, lists, item_start, segs, seg_cnt, tile_pre, part_pre, seg_ord, splits, table, keys_a,
+  size_t header, lists, item_start, segs, seg_cnt, tile_pre, part_pre, seg_ord, table, keys_a,
       keys_b, idx_a, idx_b, trec, tlen, total;
   uint64_t cap, items_max;
 };
@@ -82,10 +82,6 @@ constexpr ManyLayout many_layout_cap(uint64_t cap, uint32_t W, uint32_t n_lists)
   o += align_up(4 * (S + 1), 256);
   l.seg_ord = o;
   o += align_up(4 * S, 256);
-  // merge-path splits of one pass: two per partition (at least 64 elements
-  // each, plus one partial partition per segment)
-  l.splits = o;
-  o += align_up(4 * 2 * (cap / 64 + S + 1), 256);
   l.table = o;
   o += align_up(4 * l.items_max * (W + 1), 256);
   l.keys_a = o;
@@ -155,7 +151,6 @@ Many many_view(void* base, size_t ws_bytes, uint32_t W, uint32_t n_lists, const 
   m.ws.wait_polls = first_wait_polls();
   m.ws.hdr = reinterpret_cast<WsHeader*>(b + l.header + 256);
   m.ws.table = m.table;
-  m.ws.splits = reinterpret_cast<uint32_t*>(b + l.splits);
   m.ws.autoa = nullptr;
   m.ws.keys[0] = reinterpret_cast<uint64_t*>(b + l.keys_a);
   m.ws.keys[1] = reinterpret_cast<uint64_t*>(b + l.keys_b);
@@ -182,55 +177,6 @@ __device__ __forceinline__ uint32_t upper_index(const uint32_t* a, uint32_t n, u
   return lo;
 }
 
-// Exclusive scan of f(0..n-1) by one block into out[0..n]; returns the total.
-template <typename F>
-__device__ uint32_t block_scan_into(uint32_t n, F f, uint32_t* out) {
-  // chunks of kScanChunk values: read with coalesced accesses (all of a
-  // thread's reads in flight together) into shared memory, scanned there,
-  // written back coalesced; a running carry joins the chunks
-  constexpr uint32_t kScanChunk = 8192;
-  constexpr uint32_t kPer = kScanChunk / 1024;
-  __shared__ uint32_t tmp[1024 / 32 + 1];
-  __shared__ uint32_t chunk[kScanChunk];
-  uint32_t carry = 0;
-  for (uint32_t c0 = 0; c0 < n; c0 += kScanChunk) {
-    const uint32_t m = min(kScanChunk, n - c0);
-    uint32_t vals[kPer];
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-      const uint32_t i = k * blockDim.x + threadIdx.x;
-      vals[k] = i < m ? f(c0 + i) : 0u;
-    }
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-      const uint32_t i = k * blockDim.x + threadIdx.x;
-      if (i < kScanChunk) chunk[i] = vals[k];
-    }
-    __syncthreads();
-    // thread t scans positions t kPer .. t kPer + kPer - 1 of the chunk
-    uint32_t mine[kPer], s = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-      const uint32_t i = threadIdx.x * kPer + k;
-      mine[k] = i < kScanChunk ? chunk[i] : 0u;
-      s += mine[k];
-    }
-    uint32_t tot;
-    uint32_t run = carry + block_exclusive_scan(s, tmp, &tot);
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-      const uint32_t i = threadIdx.x * kPer + k;
-      if (i < kScanChunk) chunk[i] = run;
-      run += mine[k];
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) out[c0 + i] = chunk[i];
-    carry += tot;
-    __syncthreads();  // the chunk is reused
-  }
-  if (threadIdx.x == 0) out[n] = carry;
-  return carry;
-}
 
 __device__ __forceinline__ const uint8_t* len_of(const Many& m, const uint8_t* len, int text) {
   return text ? m.tlen : len;
@@ -323,7 +269,7 @@ __global__ void __launch_bounds__(1024) many_plan_kernel(Many m, uint32_t max_li
   __syncthreads();
   const uint32_t tot = block_scan_into(
       m.n_lists, [&](uint32_t i) { return (m.ls[i].n + kItemWords - 1) / kItemWords; },
-      m.item_start);
+      m.item_start, m.item_start + m.n_lists);
   if (threadIdx.x == 0) m.hdr->items = tot;
 }
 
@@ -365,45 +311,37 @@ many_hist_kernel(const uint8_t* __restrict__ len_in, int text, Many m) {
   }
 }
 
-// Per list: L-major exclusive scan over (length, item) counts -> scatter
-// bases (global positions), bucket offsets, segment table.
+// Per list, one warp: L-major exclusive scan over (length, item) counts ->
+// scatter bases (global positions), bucket offsets, segment table.  A list's
+// items are scanned 32 at a time with shuffles, so no block barrier is needed.
 __global__ void __launch_bounds__(kThreads)
 many_lscan_kernel(Many m, uint32_t* __restrict__ out_off) {
-  __shared__ uint32_t tmp[kWarps + 1];
-  __shared__ uint32_t s_carry;
-  const uint32_t W = m.W;
-  for (uint32_t i = blockIdx.x; i < m.n_lists; i += gridDim.x) {
+  const uint32_t W = m.W, lane = lane_id();
+  const uint32_t warps = gridDim.x * kWarps;
+  for (uint32_t i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < m.n_lists; i += warps) {
     const uint32_t it0 = m.item_start[i], ni = m.item_start[i + 1] - it0;
     const uint64_t woff = m.lists[i].word_off;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
+    uint32_t carry = 0;
     for (uint32_t L = 0; L <= W; ++L) {
-      // scan this length's counts over the list's items, in chunks of kThreads
-      uint32_t first = s_carry;
-      __syncthreads();
-      for (uint32_t c0 = 0; c0 < ni; c0 += kThreads) {
-        const uint32_t c = c0 + threadIdx.x;
+      const uint32_t first = carry;
+      for (uint32_t c0 = 0; c0 < ni; c0 += 32) {
+        const uint32_t c = c0 + lane;
         const uint64_t e = static_cast<uint64_t>(it0 + c) * (W + 1) + L;
         const uint32_t v = c < ni ? m.table[e] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(v, tmp, &tot);
-        if (c < ni) m.table[e] = static_cast<uint32_t>(woff) + s_carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += tot;
-        __syncthreads();
+        const uint32_t inc = warp_inclusive_scan(v);
+        if (c < ni) m.table[e] = static_cast<uint32_t>(woff) + carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
       }
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         if (out_off) out_off[static_cast<uint64_t>(i) * (W + 2) + L] = first;
         if (L >= 1) {
-          const uint32_t s = i * W + (L - 1);
-          m.seg_start[s] = static_cast<uint32_t>(woff) + first;
-          m.seg_cnt[s] = s_carry - first;
+          const uint32_t sg = i * W + (L - 1);
+          m.seg_start[sg] = static_cast<uint32_t>(woff) + first;
+          m.seg_cnt[sg] = carry - first;
         }
       }
-      __syncthreads();
     }
-    if (threadIdx.x == 0 && out_off) out_off[static_cast<uint64_t>(i) * (W + 2) + W + 1] = s_carry;
-    __syncthreads();
+    if (lane == 0 && out_off) out_off[static_cast<uint64_t>(i) * (W + 2) + W + 1] = carry;
   }
 }
 
@@ -483,7 +421,7 @@ __global__ void __launch_bounds__(1024) many_tplan_kernel(Many m) {
         const uint32_t c = m.seg_cnt[s];
         return c <= kWarpSortMax ? 0u : (c + T - 1) / T;
       },
-      m.tile_pre);
+      m.tile_pre, m.tile_pre + S);
   if (threadIdx.x == 0) m.hdr->tiles = tot;
 }
 
@@ -632,7 +570,7 @@ __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m) {
         const uint32_t sg = m.seg_ord[j], P = merge_part_for(m.part, keys_for_len(sg % m.W + 1));
         return (m.seg_cnt[sg] + P - 1) / P;
       },
-      m.part_pre);
+      m.part_pre, m.part_pre + active);
   __syncthreads();
   if (threadIdx.x < kMaxPasses) {
     // segments with more than p passes: the first sum(hist[c], c > p)
@@ -642,30 +580,11 @@ __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m) {
   }
 }
 
-// The split of every partition of one merge pass, one warp per partition.
-__global__ void __launch_bounds__(256) many_split_kernel(Many m, uint32_t pass, uint32_t R, int src) {
-  const uint32_t parts = m.hdr->pass_parts[pass], active = m.hdr->active;
-  const uint32_t warps = gridDim.x * (blockDim.x / 32);
-  for (uint32_t p = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); p < parts; p += warps) {
-    const uint32_t j = upper_index(m.part_pre, active + 1, p), s = m.seg_ord[j];
-    const uint32_t L = s % m.W + 1;
-    const uint32_t P = merge_part_for(m.part, keys_for_len(L));
-    const uint32_t o0 = (p - m.part_pre[j]) * P;
-    const uint32_t bstart = m.seg_start[s], cnt = m.seg_cnt[s];
-    uint32_t* out = m.ws.splits + p;
-    switch (keys_for_len(L)) {
-      case 1: merge_split_warp<1>(bstart, cnt, R, o0, src, m.ws, out); break;
-      case 2: merge_split_warp<2>(bstart, cnt, R, o0, src, m.ws, out); break;
-      case 3: merge_split_warp<3>(bstart, cnt, R, o0, src, m.ws, out); break;
-      default: merge_split_warp<4>(bstart, cnt, R, o0, src, m.ws, out); break;
-    }
-  }
-}
-
-// One merge pass over the partitions of every segment longer than R, each
-// persistent CTA's inputs staged by bulk copies one partition ahead
-// (merge_pass_staged).
-__global__ void __launch_bounds__(256) many_merge_kernel(Many m, uint32_t pass, uint32_t R, int src) {
+// One merge pass over the partitions of every segment longer than R, in
+// contiguous chunks per persistent CTA (merge_pass_ws: a producer warp finds
+// the splits, short searches over runs of at most one list's segment, and
+// stages the inputs by bulk copies; the consumer warps merge).
+__global__ void __launch_bounds__(kMergeThreads) many_merge_kernel(Many m, uint32_t pass, uint32_t R, int src) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t active = m.hdr->active;
   const auto part_of = [&](uint32_t p, uint32_t* K, uint32_t* P, uint32_t* bstart, uint32_t* cnt, uint32_t* o0) {
@@ -676,7 +595,7 @@ __global__ void __launch_bounds__(256) many_merge_kernel(Many m, uint32_t pass, 
     *bstart = m.seg_start[s];
     *cnt = m.seg_cnt[s];
   };
-  merge_pass_staged(align128(smem), m.part, m.hdr->pass_parts[pass], R, src, m.ws, part_of);
+  merge_pass_ws(align128(smem), m.part, m.hdr->pass_parts[pass], R, src, m.ws, nullptr, part_of);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -764,7 +683,7 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   if (e != cudaSuccess) return e;
   const uint32_t grid = static_cast<uint32_t>(sms) * 4;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, many_merge_kernel, 256, msm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, many_merge_kernel, kMergeThreads, msm);
   if (e != cudaSuccess) return e;
   // persistent merge CTAs: as many as fit the SMs
   const uint32_t mgrid = static_cast<uint32_t>(sms) * (occ < 1 ? 1u : occ > 8 ? 8u : static_cast<uint32_t>(occ));
@@ -782,8 +701,8 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   if (p.tile < max_list_words) BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m);
   uint32_t pass = 0;
   for (uint64_t R = p.tile; R < max_list_words && pass < kMaxPasses; R <<= 1, ++pass) {
-    BSORT_LAUNCH("many_split", many_split_kernel, grid * 2, 256, 0, s, m, pass, static_cast<uint32_t>(R), src);
-    BSORT_LAUNCH("many_merge", many_merge_kernel, mgrid, 256, msm, s, m, pass, static_cast<uint32_t>(R), src);
+    BSORT_LAUNCH("many_merge", many_merge_kernel, mgrid, kMergeThreads, msm, s, m, pass, static_cast<uint32_t>(R),
+                 src);
     src ^= 1;
   }
   BSORT_LAUNCH("many_gather", many_gather_kernel, grid, kThreads, 0, s, m, out_off, out_rec, out_perm);

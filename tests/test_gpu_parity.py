@@ -147,6 +147,25 @@ def test_sort_high_bytes(env, alg):
     assert_same_answer(out_rec, out_perm, off, expect, n)
 
 
+@pytest.mark.parametrize("alg", ["merge", "auto"])
+@pytest.mark.parametrize("stray", [None, b"@", b"[", b"`", b"{"])
+def test_seven_and_eight_byte_words(env, alg, stray):
+    """Tiles of 7- and 8-byte one-key words sort on 6-bit letter codes when
+    every word of the tile is letters only, else on the raw keys; bytes just
+    outside the letter ranges put some tiles on the raw path."""
+    torch, bs, orc = env
+    n, W = 60_000, 16
+    rec, ln = table(91, n, W, b"aAzZmMbY", 8, 7)
+    if stray is not None:
+        rng = np.random.default_rng(92)
+        rows = rng.choice(n, size=12, replace=False)
+        rec[rows, rng.integers(0, 7, size=12)] = stray[0]
+    expect = orc.stable_sort(orc.Words(rec, ln))
+    s, out_rec, out_perm, off = run_records(env, rec, ln, alg)
+    assert s.status() == 0
+    assert_same_answer(out_rec, out_perm, off, expect, n)
+
+
 @pytest.mark.parametrize("alg", ALGS)
 def test_single_big_bucket_forces_merges(env, alg):
     torch, bs, orc = env
