@@ -287,10 +287,19 @@ many_hist_kernel(const uint8_t* __restrict__ len_in, int text, Many m) {
     const uint32_t n = m.ls[i].n;
     const uint32_t j0 = (it - m.item_start[i]) * kItemWords, j1 = min(n, j0 + kItemWords);
     bool bad_zero = false, bad_long = false;
-    for (uint32_t b = j0; b < j1; b += kThreads) {
-      const uint32_t j = b + threadIdx.x;
-      uint32_t L = j < j1 ? len[off + j] : 0u;
-      if (j < j1) {
+    // all of a thread's lengths of the item are loaded before any is counted,
+    // so their loads are in flight together
+    constexpr uint32_t kPer = kItemWords / kThreads;
+    uint32_t Ls[kPer];
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      const uint32_t j = j0 + k * kThreads + threadIdx.x;
+      Ls[k] = j < j1 ? len[off + j] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+      uint32_t L = Ls[k];
+      if (L != 0xFFFFFFFFu) {
         bad_zero |= L == 0;
         bad_long |= L > W;
       }
@@ -368,17 +377,31 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
       for (uint32_t k = lane; k < kBins; k += 32) wcnt[warp][k] = 0;
       __syncwarp();
       uint32_t Ls[kItems], rank[kItems];
+      // lengths, then the record words of the chunk: all loads in flight
+      // together, ahead of the ranking
+      uint64_t words[kItems][kMaxW / 8];
 #pragma unroll
       for (uint32_t u = 0; u < kItems; ++u) {
         const uint32_t j = c + warp * 32 * kItems + u * 32 + lane;
         uint32_t L = j < j1 ? len[off + j] : 0u;
-        if (L > W) L = 0;
+        Ls[u] = L > W ? 0u : L;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kItems; ++u) {
+        const uint32_t j = c + warp * 32 * kItems + u * 32 + lane;
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + (off + j) * W);
+        const uint32_t K = Ls[u] ? keys_for_len(Ls[u]) : 0u;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxW / 8; ++k) words[u][k] = k < K ? __ldg(src + k) : 0ull;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kItems; ++u) {
+        const uint32_t L = Ls[u];
         const uint32_t peers = __match_any_sync(0xffffffffu, L);
         rank[u] = wcnt[warp][L] + __popc(peers & lanemask_lt());
         __syncwarp();
         if (lane == __ffs(peers) - 1) wcnt[warp][L] += __popc(peers);
         __syncwarp();
-        Ls[u] = L;
       }
       __syncthreads();
       if (threadIdx.x <= W) {
@@ -398,10 +421,10 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
         if (L == 0) continue;
         const uint32_t j = c + warp * 32 * kItems + u * 32 + lane;
         const uint32_t pos = wcnt[warp][L] + rank[u];
-        const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + (off + j) * W);
         const uint32_t K = keys_for_len(L);
-        for (uint32_t k = 0; k < KW; ++k)
-          if (k < K) ws.keys[0][k * ws.cap + pos] = bswap64(__ldg(src + k)) & key_mask(L, k);
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxW / 8; ++k)
+          if (k < K) ws.keys[0][k * ws.cap + pos] = bswap64(words[u][k]) & key_mask(L, k);
         ws.idx[0][pos] = j;
       }
       __syncthreads();
@@ -616,25 +639,44 @@ many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __rest
     __syncthreads();
     const uint32_t n = s_off[W + 1];
     const uint32_t j0 = (it - m.item_start[i]) * kItemWords, j1 = min(n, j0 + kItemWords);
-    for (uint32_t r = j0 + threadIdx.x; r < j1; r += kThreads) {
-      uint32_t L = 1;
-      {
-        uint32_t lo = 1, hi = W;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= r) lo = mid;
-          else hi = mid - 1;
+    // four positions per thread at a time: all their loads in flight before
+    // the stores
+    constexpr uint32_t kG = 4;
+    for (uint32_t r0 = j0 + threadIdx.x; r0 < j1; r0 += kG * kThreads) {
+      uint64_t w[kG][kMaxW / 8];
+      uint32_t pm[kG], Ks[kG];
+#pragma unroll
+      for (uint32_t u = 0; u < kG; ++u) {
+        const uint32_t r = r0 + u * kThreads;
+        Ks[u] = 0;
+        pm[u] = 0;
+        if (r < j1) {
+          uint32_t lo = 1, hi = W;  // the length L with s_off[L] <= r < s_off[L + 1]
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= r) lo = mid;
+            else hi = mid - 1;
+          }
+          Ks[u] = keys_for_len(lo);
+          const uint64_t g = off + r;
+          const uint64_t* kb = s_buf[lo] ? ws.keys[1] : ws.keys[0];
+          const uint32_t* ib = s_buf[lo] ? ws.idx[1] : ws.idx[0];
+#pragma unroll
+          for (uint32_t k = 0; k < kMaxW / 8; ++k) w[u][k] = k < Ks[u] ? __ldg(kb + k * ws.cap + g) : 0ull;
+          pm[u] = __ldg(ib + g);
         }
-        L = lo;
       }
-      const uint32_t K = keys_for_len(L);
-      const int buf = static_cast<int>(s_buf[L]);
-      const uint64_t g = off + r;
-      const uint64_t* kb = buf ? ws.keys[1] : ws.keys[0];
-      const uint32_t* ib = buf ? ws.idx[1] : ws.idx[0];
-      uint64_t* dst = reinterpret_cast<uint64_t*>(out_rec + g * W);
-      for (uint32_t k = 0; k < KW; ++k) dst[k] = k < K ? bswap64(kb[k * ws.cap + g]) : 0ull;
-      out_perm[g] = ib[g];
+#pragma unroll
+      for (uint32_t u = 0; u < kG; ++u) {
+        const uint32_t r = r0 + u * kThreads;
+        if (r >= j1) continue;
+        const uint64_t g = off + r;
+        uint64_t* dst = reinterpret_cast<uint64_t*>(out_rec + g * W);
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxW / 8; ++k)
+          if (k < KW) dst[k] = k < Ks[u] ? bswap64(w[u][k]) : 0ull;
+        out_perm[g] = pm[u];
+      }
     }
     __syncthreads();
   }

@@ -96,3 +96,25 @@ def test_text_matches_oracle(env):
         assert n == w.n
         assert np.array_equal(u32(out_perm[:n]), expect.out_perm)
         assert np.array_equal(out_rec[:n].cpu().numpy(), expect.out_rec)
+
+
+@pytest.mark.parametrize("W", [8, 24])
+def test_permutation_output_off_16_byte_boundary(env, W):
+    """The merge levels stage permutation ranges from the 16-byte boundary at
+    or below their first entry, so a permutation array that starts 4 bytes
+    past a boundary (only 4-byte alignment is required of it) still gives the
+    oracle's answer; W = 8 and 24 put odd records off 16-byte boundaries."""
+    torch, bs, orc = env
+    n = 40_000
+    rec, ln = table(300 + W, n, W, b"abcdefgh")
+    w = orc.Words(rec, ln)
+    expect = orc.stable_sort_whole(w)
+    s = bs.Sorter(n, W)
+    perm_buf = torch.empty(n + 4, dtype=torch.int32, device="cuda")
+    out_perm = perm_buf[1:n + 1]
+    bs._lib.bsort_sort_records_whole(to_dev(rec, torch), to_dev(ln, torch), n, W, "auto", None, s.out_rec,
+                                     out_perm, s.ws, s.ws_bytes)
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    assert np.array_equal(u32(out_perm), expect.out_perm)
+    assert np.array_equal(s.out_rec[:n].cpu().numpy(), expect.out_rec)
