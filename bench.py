@@ -40,16 +40,19 @@ NCU_TRAFFIC = {
     # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
-    "auto_segsort": {"bytes": 4 * (60.69e6 + 126.21e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "f70b5c4f2307",
-                                 "paper_1411_5283_gb300/csrc/common.cuh": "e41e15ea3b9c",
-                                 "paper_1411_5283_gb300/csrc/sort_impl.cuh": "17574389fb25"}},
-    "auto_partition": {"bytes": 4 * (27.57e6 + 1.22e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "f70b5c4f2307",
-                                   "paper_1411_5283_gb300/csrc/common.cuh": "e41e15ea3b9c"}},
-    "auto_bucket": {"bytes": 4 * (138.94e6 + 23.28e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "f70b5c4f2307",
-                                "paper_1411_5283_gb300/csrc/common.cuh": "e41e15ea3b9c"}},
+    "auto_segsort": {"bytes": 4 * (60.95e6 + 126.99e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "b4b9f65223b0",
+                                 "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
+                                 "paper_1411_5283_gb300/csrc/sort_impl.cuh": "91812a4d58a1",
+                                 "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
+    "auto_partition": {"bytes": 4 * (55.23e6 + 2.84e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "b4b9f65223b0",
+                                   "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
+                                   "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
+    "auto_bucket": {"bytes": 4 * (138.91e6 + 23.33e6),
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "b4b9f65223b0",
+                                "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
+                                "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
 }
 
 
@@ -75,6 +78,7 @@ def parse():
     ap.add_argument("--alg", default="auto")
     ap.add_argument("--words", type=int, default=N_WORDS)
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--e2e-depth", type=int, default=2, help="slots of the end-to-end host pipeline")
     ap.add_argument("--workload", choices=["large", "batched", "served", "text", "whole", "packed"],
                     default="large",
                     help="large: 16.7M pre-tokenised words (default, the headline line); "
@@ -257,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
     # on two slots (streams, buffers, workspaces), so one step's copy-in, the
     # previous step's sort and the one before's copy-out overlap on the GPU
     from paper_1411_5283_gb300.pipeline import HostPipeline
-    depth = 2
+    depth = args.e2e_depth
     pipe = HostPipeline(n, W, depth=depth, device=str(dev))
     outs_h = [(torch.empty((n, W), dtype=torch.uint8).pin_memory(),
                torch.empty(n, dtype=torch.int32).pin_memory(),
@@ -838,7 +842,7 @@ def main():
                     "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                     "ms_per_step": round(r["e2e_ms"], 4),
                     "how": "pinned host table in, answer out, every step; consecutive steps "
-                           "on two streams (HostPipeline) so copies and sorts overlap"},
+                           f"on {args.e2e_depth} slots (HostPipeline streams) so copies and sorts overlap"},
             "e2e_packed": {"value": round(replicas.throughput(n_total, r["e2e_packed_ms"]), 2),
                            "unit": "Mwords/s", "h2d_bytes_per_step": r["h2d"],
                            "d2h_bytes_per_step": r["d2h_packed"],

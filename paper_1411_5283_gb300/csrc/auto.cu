@@ -368,12 +368,9 @@ __device__ void sort_sample_chunk(uint8_t* smem, const AutoView& v, const Bucket
 __global__ void __launch_bounds__(1024)
 auto_spl_sort_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ BucketPlan p;
   const AutoView& v = av;
   const uint32_t L = blockIdx.x + 1, j = blockIdx.y;
-  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
-  __syncthreads();
   if (threadIdx.x == 0) {
     p = v.hdr->plans[L];
     if (L == W && j == 0) {
@@ -493,12 +490,9 @@ __device__ void select_splitters(uint8_t* smem, const AutoView& v, const BucketP
 __global__ void __launch_bounds__(1024)
 auto_spl_select_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ BucketPlan p;
   const AutoView& v = av;
   const uint32_t L = blockIdx.x + 1, j = blockIdx.y;
-  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
-  __syncthreads();
   if (threadIdx.x == 0) p = v.hdr->plans[L];
   __syncthreads();
   if (p.g < 2) return;
@@ -591,12 +585,9 @@ __device__ void segment_codes(const AutoView& v, const BucketPlan& p, uint32_t L
 constexpr uint32_t kSplDirCtas = 4;
 __global__ void __launch_bounds__(288)
 auto_spl_dir_kernel(const uint32_t* __restrict__ d_off, uint32_t W, Ws ws, AutoView av) {
-  __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ BucketPlan p;
   const AutoView& v = av;
   const uint32_t L = blockIdx.x + 1;
-  if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
-  __syncthreads();
   if (threadIdx.x == 0) p = v.hdr->plans[L];
   __syncthreads();
   if (p.K <= 2) segment_codes(v, p, L);

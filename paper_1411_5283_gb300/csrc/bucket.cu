@@ -80,23 +80,36 @@ scatter_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
   const uint32_t start = blockIdx.x * wpb;
   const uint32_t end = min(n, start + wpb);
   if (threadIdx.x <= W) cursor[threadIdx.x] = base_tab[threadIdx.x * G + blockIdx.x];
-  const uint32_t KW = W / 8;
   for (uint32_t c = start; c < end; c += kThreads * kItems) {
     for (uint32_t i = lane; i < kBins; i += 32) wcnt[warp][i] = 0;
     __syncwarp();
     uint32_t Ls[kItems], rank[kItems];
-    // warp `warp` owns words [c + warp*32*kItems, +32*kItems), kItems steps of 32
+    // warp `warp` owns words [c + warp*32*kItems, +32*kItems), kItems steps of
+    // 32; the lengths, then the record words, are all loaded before the
+    // ranking, so the loads are in flight together
+    uint64_t words[kItems][kMaxW / 8];
 #pragma unroll
     for (uint32_t it = 0; it < kItems; ++it) {
       const uint32_t i = c + warp * 32 * kItems + it * 32 + lane;
-      uint32_t L = i < end ? len[i] : 0u;
-      if (L > W) L = 0;
+      const uint32_t L = i < end ? len[i] : 0u;
+      Ls[it] = L > W ? 0u : L;
+    }
+#pragma unroll
+    for (uint32_t it = 0; it < kItems; ++it) {
+      const uint32_t i = c + warp * 32 * kItems + it * 32 + lane;
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
+      const uint32_t K = Ls[it] ? keys_for_len(Ls[it]) : 0u;
+#pragma unroll
+      for (uint32_t k = 0; k < kMaxW / 8; ++k) words[it][k] = k < K ? __ldg(src + k) : 0ull;
+    }
+#pragma unroll
+    for (uint32_t it = 0; it < kItems; ++it) {
+      const uint32_t L = Ls[it];
       const uint32_t peers = __match_any_sync(0xffffffffu, L);
       rank[it] = wcnt[warp][L] + __popc(peers & lanemask_lt());
       __syncwarp();
       if (lane == __ffs(peers) - 1) wcnt[warp][L] += __popc(peers);
       __syncwarp();
-      Ls[it] = L;
     }
     __syncthreads();
     if (threadIdx.x <= W) {
@@ -116,11 +129,10 @@ scatter_kernel(const uint8_t* __restrict__ rec, const uint8_t* __restrict__ len,
       if (L == 0) continue;
       const uint32_t i = c + warp * 32 * kItems + it * 32 + lane;
       const uint32_t pos = wcnt[warp][L] + rank[it];
-      const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + static_cast<uint64_t>(i) * W);
       const uint32_t K = keys_for_len(L);
-      for (uint32_t k = 0; k < KW; ++k) {
-        if (k < K) ws.keys[0][k * ws.cap + pos] = bswap64(__ldg(src + k)) & key_mask(L, k);
-      }
+#pragma unroll
+      for (uint32_t k = 0; k < kMaxW / 8; ++k)
+        if (k < K) ws.keys[0][k * ws.cap + pos] = bswap64(words[it][k]) & key_mask(L, k);
       ws.idx[0][pos] = i;
     }
     __syncthreads();

@@ -127,7 +127,7 @@ merge_split_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t R, u
 __global__ void __launch_bounds__(kMergeThreads) merge_pass_kernel(const uint32_t* __restrict__ d_off, uint32_t W,
                                                                    uint32_t R, uint32_t part, int src, Ws ws,
                                                                    int presplit) {
-  extern __shared__ __align__(128) uint8_t smem[];
+  extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint32_t s_off[kMaxW + 2], s_pre[kMaxW + 2];
   if (threadIdx.x < W + 2) s_off[threadIdx.x] = d_off[threadIdx.x];
   __syncthreads();

@@ -363,7 +363,7 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
   __shared__ uint32_t wcnt[kWarps][kBins];
   const uint8_t* len = len_of(m, len_in, text);
   const uint8_t* rec = rec_of(m, rec_in, text);
-  const uint32_t W = m.W, KW = W / 8, warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t W = m.W, warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t items = m.hdr->items;
   const Ws& ws = m.ws;
   for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(1024) many_pplan_kernel(Many m) {
 // the splits, short searches over runs of at most one list's segment, and
 // stages the inputs by bulk copies; the consumer warps merge).
 __global__ void __launch_bounds__(kMergeThreads) many_merge_kernel(Many m, uint32_t pass, uint32_t R, int src) {
-  extern __shared__ __align__(128) uint8_t smem[];
+  extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t active = m.hdr->active;
   const auto part_of = [&](uint32_t p, uint32_t* K, uint32_t* P, uint32_t* bstart, uint32_t* cnt, uint32_t* o0) {
     const uint32_t j = upper_index(m.part_pre, active + 1, p), s = m.seg_ord[j];
