@@ -212,11 +212,33 @@ __device__ WholeGeo whole_issue(uint8_t* buf, uint32_t W, uint32_t P, const Whol
   return g;
 }
 
-// A staged record as big-endian key words.
+// A staged record as big-endian key words (16-byte loads when W is a multiple
+// of 16: every staged record then starts on a 16-byte boundary).
 template <int KW>
 __device__ __forceinline__ void staged_key(const uint8_t* p, uint64_t (&k)[KW]) {
+  if constexpr (KW % 2 == 0) {
 #pragma unroll
-  for (int j = 0; j < KW; ++j) k[j] = bswap64(reinterpret_cast<const uint64_t*>(p)[j]);
+    for (int j = 0; j < KW; j += 2) {
+      const ulonglong2 v = reinterpret_cast<const ulonglong2*>(p)[j / 2];
+      k[j] = bswap64(v.x);
+      k[j + 1] = bswap64(v.y);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KW; ++j) k[j] = bswap64(reinterpret_cast<const uint64_t*>(p)[j]);
+  }
+}
+
+// Writes key words k back as a record at p (16-byte stores when KW is even).
+template <int KW>
+__device__ __forceinline__ void put_record(uint64_t* p, const uint64_t (&k)[KW]) {
+  if constexpr (KW % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < KW; j += 2) reinterpret_cast<ulonglong2*>(p)[j / 2] = make_ulonglong2(bswap64(k[j]), bswap64(k[j + 1]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < KW; ++j) p[j] = bswap64(k[j]);
+  }
 }
 
 // Merges a staged unit into `out` (thread t produces outputs [t per, t per +
@@ -253,25 +275,30 @@ __device__ void whole_merge_staged(const uint8_t* buf, uint8_t* out, const Whole
   for (uint32_t o = o0; o < o1; ++o) {
     const bool takeA = ib >= g.cb || (ia < g.ca && !key_less<KW>(kb, ka));
     if (takeA) {
-#pragma unroll
-      for (int j = 0; j < KW; ++j) orec[o * KW + j] = bswap64(ka[j]);
+      put_record<KW>(orec + o * KW, ka);
       operm[o] = permA(ia);
       if (++ia < g.ca) staged_key<KW>(recA(ia), ka);
     } else {
-#pragma unroll
-      for (int j = 0; j < KW; ++j) orec[o * KW + j] = bswap64(kb[j]);
+      put_record<KW>(orec + o * KW, kb);
       operm[o] = permB(ib);
       if (++ib < g.cb) staged_key<KW>(recB(ib), kb);
     }
   }
   __syncthreads();
   uint64_t* drec = reinterpret_cast<uint64_t*>(dst_rec) + g.out0 * KW;
-  for (uint32_t q = threadIdx.x; q < tot * KW; q += blockDim.x) drec[q] = orec[q];
+  if constexpr (KW % 2 == 0) {
+    // the output records start on 16-byte boundaries: 16-byte stores
+    ulonglong2* d2 = reinterpret_cast<ulonglong2*>(drec);
+    const ulonglong2* o2 = reinterpret_cast<const ulonglong2*>(orec);
+    for (uint32_t q = threadIdx.x; q < tot * KW / 2; q += blockDim.x) d2[q] = o2[q];
+  } else {
+    for (uint32_t q = threadIdx.x; q < tot * KW; q += blockDim.x) drec[q] = orec[q];
+  }
   for (uint32_t e = threadIdx.x; e < tot; e += blockDim.x) dst_perm[g.out0 + e] = operm[e];
 }
 
 template <int KW>
-__global__ void __launch_bounds__(kWholeThreads)
+__global__ void __launch_bounds__(kWholeThreads, 4)
 whole_merge_kernel(const uint32_t* __restrict__ d_off, uint32_t W, uint32_t span,
                    const uint8_t* __restrict__ src_rec, const uint32_t* __restrict__ src_perm,
                    uint8_t* __restrict__ dst_rec, uint32_t* __restrict__ dst_perm,

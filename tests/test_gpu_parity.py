@@ -149,17 +149,19 @@ def test_sort_high_bytes(env, alg):
 
 @pytest.mark.parametrize("alg", ["merge", "auto"])
 @pytest.mark.parametrize("stray", [None, b"@", b"[", b"`", b"{"])
-def test_seven_and_eight_byte_words(env, alg, stray):
-    """Tiles of 7- and 8-byte one-key words sort on 6-bit letter codes when
+@pytest.mark.parametrize("lens", [(7, 8), (13, 16)])
+def test_letter_coded_tiles(env, alg, stray, lens):
+    """Tiles of 7- or 8-byte one-key words sort on 6-bit letter codes when
     every word of the tile is letters only, else on the raw keys; bytes just
-    outside the letter ranges put some tiles on the raw path."""
+    outside the letter ranges put some tiles on the raw path.  Two-key words of
+    13 to 16 bytes with the same strays check the (keys, index) network."""
     torch, bs, orc = env
     n, W = 60_000, 16
-    rec, ln = table(91, n, W, b"aAzZmMbY", 8, 7)
+    rec, ln = table(91 + lens[0], n, W, b"aAzZmMbY", lens[1], lens[0])
     if stray is not None:
         rng = np.random.default_rng(92)
         rows = rng.choice(n, size=12, replace=False)
-        rec[rows, rng.integers(0, 7, size=12)] = stray[0]
+        rec[rows, rng.integers(0, lens[0], size=12)] = stray[0]
     expect = orc.stable_sort(orc.Words(rec, ln))
     s, out_rec, out_perm, off = run_records(env, rec, ln, alg)
     assert s.status() == 0
