@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--alg", default="auto")
     ap.add_argument("--words", type=int, default=N_WORDS)
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--e2e-depth", type=int, default=2, help="slots of the end-to-end host pipeline")
+    ap.add_argument("--e2e-depth", type=int, default=3, help="slots of the end-to-end host pipeline")
     ap.add_argument("--workload", choices=["large", "batched", "served", "text", "whole", "packed"],
                     default="large",
                     help="large: 16.7M pre-tokenised words (default, the headline line); "
@@ -258,8 +258,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the C ABI with host buffers -------------------
     # every step copies its input table in from pinned host memory and its
     # answer (records, permutation, offsets) back out; consecutive steps run
-    # on two slots (streams, buffers, workspaces), so one step's copy-in, the
-    # previous step's sort and the one before's copy-out overlap on the GPU
+    # on --e2e-depth slots (streams, buffers, workspaces), so one step's
+    # copy-in, an earlier step's sort and another's copy-out overlap on the GPU
     from paper_1411_5283_gb300.pipeline import HostPipeline
     depth = args.e2e_depth
     pipe = HostPipeline(n, W, depth=depth, device=str(dev))
