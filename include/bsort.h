@@ -20,7 +20,11 @@
  *  - Record arrays (d_rec, d_out_rec) must be 16-byte aligned.
  *  - All calls are asynchronous on stream s and return synchronously only
  *    argument errors (BSORT_E_INVALID, BSORT_E_WORKSPACE, BSORT_E_CAPACITY
- *    for host-visible sizes) or a launch failure (BSORT_E_CUDA).
+ *    for host-visible sizes) or a launch failure (BSORT_E_CUDA).  The AUTO
+ *    algorithm runs its splitter selection on a helper stream that the
+ *    library keeps per host thread and device, forked from s and joined back
+ *    into s by events within the call, so the call stays ordered with the
+ *    rest of s.
  *  - Errors found by the kernels (a word longer than W, more words than the
  *    capacity, a zero length) are recorded in a sticky status word inside the
  *    workspace; read it with bsort_get_status(), clear it with

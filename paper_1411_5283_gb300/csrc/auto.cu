@@ -2166,6 +2166,39 @@ bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W) {
          ws.cap >= static_cast<uint64_t>(n_cap) + 64 && ws.cap >= kAutoMinWords + 64;
 }
 
+namespace {
+
+// The calling host thread's helper stream on one device, with the two events
+// that fork work onto it and join it back (created on first use, kept for the
+// thread's life).  One set per thread keeps concurrent calls from different
+// threads from sharing events; calls on one thread are ordered by their
+// streams, so reusing the events is safe.
+struct SideStream {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool failed = false;
+};
+thread_local SideStream t_side[kMaxDevices];
+
+SideStream* side_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  SideStream& t = t_side[dev];
+  if (t.failed) return nullptr;
+  if (!t.side) {
+    if (cudaStreamCreateWithFlags(&t.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();  // run without the helper stream
+      t.failed = true;
+      return nullptr;
+    }
+  }
+  return &t;
+}
+
+}  // namespace
+
 cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
                         uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {
@@ -2186,18 +2219,31 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_offsets", auto_offsets_kernel, 1, 64, 0, s, W, ws, v, d_off);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_sample", auto_sample_kernel, (samples + 255) / 256, 256, 0, s, rec, len,
+  // The samples and their sort into splitters need only the bucket plans, so
+  // they run on the thread's helper stream while the bucket pass (bound by
+  // HBM) stages the words; the splitter directory needs the bucket pass's byte
+  // bounds and waits for both.
+  SideStream* ss = side_stream();
+  cudaStream_t t = s;
+  if (ss) {
+    if ((e = cudaEventRecord(ss->fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ss->side, ss->fork, 0)) != cudaSuccess) return e;
+    t = ss->side;
+  }
+  BSORT_LAUNCH("auto_sample", auto_sample_kernel, (samples + 255) / 256, 256, 0, t, rec, len,
                n_cap, d_n, W, d_off, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_bucket", auto_bucket_kernel, static_cast<uint32_t>(sms) * 2, kBucketThreads,
-               0, s, rec, len, n_cap, d_n, W, d_off, ws, v);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, s,
+  BSORT_LAUNCH("auto_spl_sort", auto_spl_sort_kernel, dim3(W, kSplChunks), 1024, kSplSortSmem, t,
                d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_select", auto_spl_select_kernel, dim3(W, kSplChunks), 1024, kSplSelectSmem,
-               s, d_off, W, ws, v);
+               t, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ss && (e = cudaEventRecord(ss->join, ss->side)) != cudaSuccess) return e;
+  BSORT_LAUNCH("auto_bucket", auto_bucket_kernel, static_cast<uint32_t>(sms) * 2, kBucketThreads,
+               0, s, rec, len, n_cap, d_n, W, d_off, ws, v);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ss && (e = cudaStreamWaitEvent(s, ss->join, 0)) != cudaSuccess) return e;
   BSORT_LAUNCH("auto_spl_dir", auto_spl_dir_kernel, dim3(W, kSplDirCtas), 288, 0, s, d_off, W, ws, v);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = partition(W, d_off, ws, v, 0, s);
