@@ -40,17 +40,17 @@ NCU_TRAFFIC = {
     # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
-    "auto_segsort": {"bytes": 4 * (60.95e6 + 126.99e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "b4b9f65223b0",
+    "auto_segsort": {"bytes": 4 * (60.66e6 + 126.03e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
                                  "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
                                  "paper_1411_5283_gb300/csrc/sort_impl.cuh": "91812a4d58a1",
                                  "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
-    "auto_partition": {"bytes": 4 * (55.23e6 + 2.84e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "b4b9f65223b0",
+    "auto_partition": {"bytes": 4 * (55.21e6 + 2.62e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
                                    "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
                                    "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
-    "auto_bucket": {"bytes": 4 * (138.91e6 + 23.33e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "b4b9f65223b0",
+    "auto_bucket": {"bytes": 4 * (138.92e6 + 23.61e6),
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
                                 "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
                                 "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
 }
