@@ -43,7 +43,7 @@ NCU_TRAFFIC = {
     "auto_segsort": {"bytes": 4 * (60.66e6 + 126.03e6),
                      "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
                                  "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
-                                 "paper_1411_5283_gb300/csrc/sort_impl.cuh": "91812a4d58a1",
+                                 "paper_1411_5283_gb300/csrc/sort_impl.cuh": "8244b70a0067",
                                  "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
     "auto_partition": {"bytes": 4 * (55.21e6 + 2.62e6),
                        "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",

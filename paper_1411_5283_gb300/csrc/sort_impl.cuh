@@ -1,7 +1,10 @@
 // Device building blocks of phase 3 (§3 Methodology, "Pre-processing", third
 // phase; §2 bubble sort; §4-§5 merge of sorted chunks), shared by the single-list
-// and the batched pipelines: shared-memory tile sorts (odd-even transposition
-// and bitonic) staged by the bulk-copy engine, and merge-path merging.
+// and the batched pipelines: tile sorts staged by the bulk-copy engine (odd-even
+// transposition in shared memory; bitonic networks in registers, one-key words
+// packed with their tile position into single 64-bit values), and merge-path
+// merge passes (a producer warp finding or reading the splits and staging the
+// inputs by bulk copies, consumer warps merging).
 #pragma once
 
 #include "common.cuh"
