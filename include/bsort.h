@@ -80,7 +80,9 @@ typedef enum { BSORT_ODD_EVEN = 0, BSORT_MERGE = 1, BSORT_AUTO = 2 } bsort_alg;
  *                     default 256 for odd-even tiles, tile / 4 for bitonic
  *                     tiles, which then hold 2, 4 or (one key word) 8
  *                     positions per thread in registers)
- *  merge_fanin        elements per merge-path partition (power of two, 512..4096)
+ *  merge_fanin        elements per merge-path partition of one-key words (power
+ *                     of two, 256..4096, default 2048); two-key words take
+ *                     half as many, three- and four-key words a quarter
  *  oddeven_cross      BSORT_MERGE (and AUTO where it takes the merge path):
  *                     the crossover between the paper's two sorts.  A length
  *                     bucket of at most this many words (1..tile) is sorted

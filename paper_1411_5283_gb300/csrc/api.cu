@@ -39,7 +39,7 @@ bsort_status check_ws(const void* d_ws, size_t ws_bytes, uint32_t W, uint64_t ne
 bool bsort::resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
   bsort_tune t{};
   if (tune) t = *tune;
-  const uint32_t KW = W / 8;
+  (void)W;  // every record width takes the same defaults
   p->alg = alg == BSORT_ODD_EVEN ? BSORT_ODD_EVEN : BSORT_MERGE;
   if (p->alg == BSORT_ODD_EVEN) {
     p->tile = t.oddeven_max ? t.oddeven_max : 512;
@@ -52,7 +52,9 @@ bool bsort::resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, So
   p->threads = t.threads_per_bucket ? t.threads_per_bucket
                                     : (p->alg == BSORT_ODD_EVEN ? 256u : (p->tile / 4 < 64 ? 64u : p->tile / 4));
   if (p->threads < 64 || p->threads > 1024 || p->threads % 32) return false;
-  p->part = t.merge_fanin ? t.merge_fanin : (KW >= 3 ? 1024u : 2048u);
+  // partitions of one-key elements; wider elements take part / 2 or part / 4
+  // (merge_part_for), so one shared-memory size serves every W
+  p->part = t.merge_fanin ? t.merge_fanin : 2048u;
   if (!pow2(p->part) || p->part < 256 || p->part > 4096) return false;
   if (2ull * p->part * 12 > 200 * 1024) return false;  // merge CTA shared memory (one-key partitions)
   if (p->part > 2 * p->tile) p->part = 2 * p->tile;  // a partition never spans two run pairs
