@@ -36,6 +36,40 @@ bsort_status check_ws(const void* d_ws, size_t ws_bytes, uint32_t W, uint64_t ne
 
 }  // namespace
 
+namespace bsort {
+
+namespace {
+
+// One set per host thread and device keeps concurrent calls from different
+// threads from sharing events; calls on one thread are ordered by their
+// streams, so reusing the events is safe.
+struct SideSlot {
+  SideStream s{};
+  bool failed = false;
+};
+thread_local SideSlot t_side[kMaxDevices];
+
+}  // namespace
+
+SideStream* side_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  SideSlot& t = t_side[dev];
+  if (t.failed) return nullptr;
+  if (!t.s.side) {
+    if (cudaStreamCreateWithFlags(&t.s.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t.s.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t.s.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();  // run without the helper stream
+      t.failed = true;
+      return nullptr;
+    }
+  }
+  return &t.s;
+}
+
+}  // namespace bsort
+
 bool bsort::resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParams* p) {
   bsort_tune t{};
   if (tune) t = *tune;

@@ -2166,39 +2166,6 @@ bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W) {
          ws.cap >= static_cast<uint64_t>(n_cap) + 64 && ws.cap >= kAutoMinWords + 64;
 }
 
-namespace {
-
-// The calling host thread's helper stream on one device, with the two events
-// that fork work onto it and join it back (created on first use, kept for the
-// thread's life).  One set per thread keeps concurrent calls from different
-// threads from sharing events; calls on one thread are ordered by their
-// streams, so reusing the events is safe.
-struct SideStream {
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  bool failed = false;
-};
-thread_local SideStream t_side[kMaxDevices];
-
-SideStream* side_stream() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-  SideStream& t = t_side[dev];
-  if (t.failed) return nullptr;
-  if (!t.side) {
-    if (cudaStreamCreateWithFlags(&t.side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();  // run without the helper stream
-      t.failed = true;
-      return nullptr;
-    }
-  }
-  return &t;
-}
-
-}  // namespace
-
 cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
                         uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {

@@ -21,6 +21,16 @@ void prof_end(cudaStream_t s);
     ::bsort::prof_end(s);                                     \
   } while (0)
 
+// The calling host thread's helper stream on the current device, with the
+// two events that fork work onto it from a call's stream and join it back
+// (created on first use, kept for the thread's life); null when they cannot
+// be created, and the caller then runs everything on its own stream.
+struct SideStream {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream* side_stream();
+
 // Geometry of the histogram / scatter grid: block b owns words [b*wpb, (b+1)*wpb).
 struct HistGeom {
   uint32_t wpb, G;

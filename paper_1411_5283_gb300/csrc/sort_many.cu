@@ -732,15 +732,29 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   BSORT_LAUNCH("many_init", many_init_kernel, 1, 1024, 0, s, m, text);
   if (text) BSORT_LAUNCH("many_tokenize", many_tok_kernel, grid, kTokThreads, 0, s, text_or_rec, m);
   BSORT_LAUNCH("many_plan", many_plan_kernel, 1, 1024, 0, s, m, max_list_words);
-  BSORT_LAUNCH("many_hist", many_hist_kernel, grid, kThreads, 0, s, len, text, m);
+  // the histogram is latency-bound at few registers: twice the CTAs per SM
+  BSORT_LAUNCH("many_hist", many_hist_kernel, grid * 2, kThreads, 0, s, len, text, m);
   BSORT_LAUNCH("many_lscan", many_lscan_kernel, grid, kThreads, 0, s, m, out_off);
+  // The tile and merge plans (one block each) need only the segment table, so
+  // they run on the thread's helper stream while the scatter moves the words;
+  // the sorts wait for both.
+  SideStream* ss = side_stream();
+  cudaStream_t t = s;
+  cudaError_t e2;
+  if (ss) {
+    if ((e2 = cudaEventRecord(ss->fork, s)) != cudaSuccess) return e2;
+    if ((e2 = cudaStreamWaitEvent(ss->side, ss->fork, 0)) != cudaSuccess) return e2;
+    t = ss->side;
+  }
+  BSORT_LAUNCH("many_tplan", many_tplan_kernel, 1, 1024, 0, t, m);
+  if (p.tile < max_list_words) BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, t, m);
+  if (ss && (e2 = cudaEventRecord(ss->join, ss->side)) != cudaSuccess) return e2;
   BSORT_LAUNCH("many_scatter", many_scatter_kernel, grid, kThreads, 0, s, text_or_rec, len, text, m);
-  BSORT_LAUNCH("many_tplan", many_tplan_kernel, 1, 1024, 0, s, m);
+  if (ss && (e2 = cudaStreamWaitEvent(s, ss->join, 0)) != cudaSuccess) return e2;
   BSORT_LAUNCH("many_small", many_small_kernel, grid, 256, 0, s, m, p.cross);
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "many_tile_odd_even" : "many_tile_bitonic", many_tile_kernel,
                grid, p.threads, tsm, s, m, p.cross);
   int src = 0;
-  if (p.tile < max_list_words) BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, s, m);
   uint32_t pass = 0;
   for (uint64_t R = p.tile; R < max_list_words && pass < kMaxPasses; R <<= 1, ++pass) {
     BSORT_LAUNCH("many_merge", many_merge_kernel, mgrid, kMergeThreads, msm, s, m, pass, static_cast<uint32_t>(R),
