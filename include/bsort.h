@@ -251,8 +251,9 @@ bsort_status bsort_sort_records_noalloc(const uint8_t* d_rec, const uint8_t* d_l
                                         uint32_t* d_off, int32_t* d_status, cudaStream_t s);
 
 /* Batched form (not in the paper; its §4 MPI chunking sorts one text): sorts
- * n_lists independent lists with one stream of persistent kernels that can be
- * captured in one CUDA graph (phases 1-3 of §3 for every list at once).
+ * n_lists independent lists with persistent kernels on stream s (two planning
+ * kernels on the thread's helper stream, forked from s and joined back) that
+ * can be captured in one CUDA graph (phases 1-3 of §3 for every list at once).
  * d_lists[n_lists] (device) describes each list.  Record mode
  * (lists_are_text = 0): d_text_or_rec / d_len hold all lists' records.  Text
  * mode: d_text_or_rec holds the texts, d_len must be NULL, and the tokenised

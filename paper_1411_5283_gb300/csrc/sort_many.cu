@@ -1,5 +1,6 @@
-// Batched form: many independent word lists sorted by one stream of
-// persistent kernels (capturable as one CUDA graph).
+// Batched form: many independent word lists sorted by persistent kernels on
+// the call's stream, two planning kernels on a helper stream forked from it
+// and joined back (capturable as one CUDA graph).
 //
 // The method of §3 Methodology, "Pre-processing" (phase 1 tokenise, phase 2
 // buckets by length, phase 3 sort each bucket, then concatenation) runs for
