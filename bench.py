@@ -108,16 +108,76 @@ def peaks():
         return 6800.0, "fallback"
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, the active
+    clock-event reasons) for the device with the given UUID; None fields when
+    the library or the device is not found."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str | None, index: int):
+        import ctypes
+        self.ok = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            r = lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) if uuid else 1
+            if r != 0 and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                return
+            self.lib, self.h, self.c = lib, h, ctypes
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+            self.ok = self.sample() is not None
+        except Exception:
+            self.ok = False
+
+    def sample(self):
+        try:
+            c = self.c
+            mhz, mx, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, c.byref(mhz)) != 0:  # 1: SM clock
+                return None
+            self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, c.byref(mx))
+            if self.reasons_fn is not None:
+                self.reasons_fn(self.h, c.byref(rs))
+            return time.perf_counter(), float(mhz.value), float(mx.value), int(rs.value)
+        except Exception:
+            return None
+
+
 class Clocks:
-    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    """Samples clocks and throttle reasons during the timed region: nvidia-smi
+    every 200 ms (the recipe's query) and, where NVML loads, an in-process
+    sampler every 2 ms, so that a region of a few tens of milliseconds still
+    gets a dozen samples; begin() / end() bracket the region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
+        import threading
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(index).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            uuid = None
+        self.nvml = _Nvml(uuid, index)
+        self.samples, self.t0, self.t1 = [], None, None
+        self.stop_flag = threading.Event()
+        self.thread = threading.Thread(target=self._poll, daemon=True) if self.nvml.ok else None
+
+    def _poll(self):
+        while not self.stop_flag.is_set():
+            smp = self.nvml.sample()
+            if smp is not None:
+                self.samples.append(smp)
+            time.sleep(0.002)
 
     def start(self):
         try:
@@ -126,11 +186,19 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        if self.thread is not None:
+            self.thread.start()
         time.sleep(0.3)
 
-    def stop(self) -> dict:
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
+
+    def _smi(self) -> dict:
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -154,6 +222,26 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+    def stop(self) -> dict:
+        smi = self._smi()
+        if self.thread is None:
+            return dict(smi, source="nvidia-smi")
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        t0 = self.t0 if self.t0 is not None else -1e30
+        t1 = self.t1 if self.t1 is not None else 1e30
+        win = [x for x in self.samples if t0 <= x[0] <= t1]
+        if not win:
+            return dict(smi, source="nvidia-smi")
+        reasons = set()
+        for _, _, _, bits in win:
+            for b, nm in _Nvml.REASONS.items():
+                if bits & b:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(x[1] for x in win), "sm_max_mhz": max(x[2] for x in win),
+                "reasons": sorted(reasons), "samples": len(win), "source": "nvml every 2 ms in the timed region",
+                "nvidia_smi": smi}
 
 
 def kernel_bytes(hist: np.ndarray, n: int, Wd: int, tile: int) -> dict:
@@ -236,11 +324,13 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.begin()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
