@@ -73,12 +73,11 @@ __device__ __forceinline__ bool key_less(const uint64_t (&a)[KW], const uint64_t
   return false;
 }
 
-// Splits: the number of elements of run A among the first d outputs of the
-// stable merge of A (na records at a) and B (nb records at b), equal records
-// taken from A first.
-// The same split found by one warp, 32 candidates a round: the predicate "A[i]
-// comes after B[d-1-i]" is false then true along i (merge_path_warp's scheme;
-// every lane of the warp calls and gets the split).
+// The split: the number of elements of run A among the first d outputs of
+// the stable merge of A (na records at a) and B (nb records at b), equal
+// records taken from A first, found by one warp, 32 candidates a round: the
+// predicate "A[i] comes after B[d-1-i]" is false then true along i (every lane
+// of the warp calls and gets the split).
 template <int KW>
 __device__ uint32_t split_global_warp(const uint8_t* rec, uint64_t a, uint32_t na, uint64_t b, uint32_t nb,
                                       uint32_t d) {
