@@ -41,16 +41,16 @@ NCU_TRAFFIC = {
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
     "auto_segsort": {"bytes": 4 * (60.66e6 + 126.03e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8db6b9708923",
                                  "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
                                  "paper_1411_5283_gb300/csrc/sort_impl.cuh": "8244b70a0067",
                                  "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
     "auto_partition": {"bytes": 4 * (55.21e6 + 2.62e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8db6b9708923",
                                    "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
                                    "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
     "auto_bucket": {"bytes": 4 * (138.92e6 + 23.61e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "2018923954e7",
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8db6b9708923",
                                 "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
                                 "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
 }

@@ -356,9 +356,12 @@ many_lscan_kernel(Many m, uint32_t* __restrict__ out_off) {
 }
 
 // Stable scatter of one item's words to their bucket positions with key packing.
+template <int KW>
 __global__ void __launch_bounds__(kThreads)
 many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restrict__ len_in,
                     int text, Many m) {
+  // KW = W / 8 key words at most per word (a template argument, so that a
+  // thread holds only the words its record width can have)
   constexpr uint32_t kItems = 4;
   __shared__ uint32_t cursor[kBins];
   __shared__ uint32_t wcnt[kWarps][kBins];
@@ -380,7 +383,7 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
       uint32_t Ls[kItems], rank[kItems];
       // lengths, then the record words of the chunk: all loads in flight
       // together, ahead of the ranking
-      uint64_t words[kItems][kMaxW / 8];
+      uint64_t words[kItems][KW];
 #pragma unroll
       for (uint32_t u = 0; u < kItems; ++u) {
         const uint32_t j = c + warp * 32 * kItems + u * 32 + lane;
@@ -393,7 +396,7 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
         const uint64_t* src = reinterpret_cast<const uint64_t*>(rec + (off + j) * W);
         const uint32_t K = Ls[u] ? keys_for_len(Ls[u]) : 0u;
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxW / 8; ++k) words[u][k] = k < K ? __ldg(src + k) : 0ull;
+        for (uint32_t k = 0; k < KW; ++k) words[u][k] = k < K ? __ldg(src + k) : 0ull;
       }
 #pragma unroll
       for (uint32_t u = 0; u < kItems; ++u) {
@@ -424,7 +427,7 @@ many_scatter_kernel(const uint8_t* __restrict__ rec_in, const uint8_t* __restric
         const uint32_t pos = wcnt[warp][L] + rank[u];
         const uint32_t K = keys_for_len(L);
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxW / 8; ++k)
+        for (uint32_t k = 0; k < KW; ++k)
           if (k < K) ws.keys[0][k * ws.cap + pos] = bswap64(words[u][k]) & key_mask(L, k);
         ws.idx[0][pos] = j;
       }
@@ -750,7 +753,12 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
   BSORT_LAUNCH("many_tplan", many_tplan_kernel, 1, 1024, 0, t, m);
   if (p.tile < max_list_words) BSORT_LAUNCH("many_pplan", many_pplan_kernel, 1, 1024, 0, t, m);
   if (ss && (e2 = cudaEventRecord(ss->join, ss->side)) != cudaSuccess) return e2;
-  BSORT_LAUNCH("many_scatter", many_scatter_kernel, grid, kThreads, 0, s, text_or_rec, len, text, m);
+  switch (KW) {
+    case 1: BSORT_LAUNCH("many_scatter", many_scatter_kernel<1>, grid, kThreads, 0, s, text_or_rec, len, text, m); break;
+    case 2: BSORT_LAUNCH("many_scatter", many_scatter_kernel<2>, grid, kThreads, 0, s, text_or_rec, len, text, m); break;
+    case 3: BSORT_LAUNCH("many_scatter", many_scatter_kernel<3>, grid, kThreads, 0, s, text_or_rec, len, text, m); break;
+    default: BSORT_LAUNCH("many_scatter", many_scatter_kernel<4>, grid, kThreads, 0, s, text_or_rec, len, text, m); break;
+  }
   if (ss && (e2 = cudaStreamWaitEvent(s, ss->join, 0)) != cudaSuccess) return e2;
   BSORT_LAUNCH("many_small", many_small_kernel, grid, 256, 0, s, m, p.cross);
   BSORT_LAUNCH(p.alg == BSORT_ODD_EVEN ? "many_tile_odd_even" : "many_tile_bitonic", many_tile_kernel,
