@@ -625,11 +625,14 @@ __global__ void __launch_bounds__(kMergeThreads) many_merge_kernel(Many m, uint3
   merge_pass_ws(align128(smem), m.part, m.hdr->pass_parts[pass], R, src, m.ws, nullptr, part_of);
 }
 
+template <int KW>
 __global__ void __launch_bounds__(kThreads)
 many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __restrict__ out_rec,
                    uint32_t* __restrict__ out_perm) {
+  // KW = W / 8 (a template argument, so that a thread holds only the key
+  // words its record width can have)
   __shared__ uint32_t s_off[kMaxW + 2], s_buf[kMaxW + 2];
-  const uint32_t W = m.W, KW = W / 8, T = m.T;
+  const uint32_t W = m.W, T = m.T;
   const uint32_t items = m.hdr->items;
   const Ws& ws = m.ws;
   for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -647,7 +650,7 @@ many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __rest
     // the stores
     constexpr uint32_t kG = 4;
     for (uint32_t r0 = j0 + threadIdx.x; r0 < j1; r0 += kG * kThreads) {
-      uint64_t w[kG][kMaxW / 8];
+      uint64_t w[kG][KW];
       uint32_t pm[kG], Ks[kG];
 #pragma unroll
       for (uint32_t u = 0; u < kG; ++u) {
@@ -666,7 +669,7 @@ many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __rest
           const uint64_t* kb = s_buf[lo] ? ws.keys[1] : ws.keys[0];
           const uint32_t* ib = s_buf[lo] ? ws.idx[1] : ws.idx[0];
 #pragma unroll
-          for (uint32_t k = 0; k < kMaxW / 8; ++k) w[u][k] = k < Ks[u] ? __ldg(kb + k * ws.cap + g) : 0ull;
+          for (uint32_t k = 0; k < KW; ++k) w[u][k] = k < Ks[u] ? __ldg(kb + k * ws.cap + g) : 0ull;
           pm[u] = __ldg(ib + g);
         }
       }
@@ -677,13 +680,25 @@ many_gather_kernel(Many m, const uint32_t* __restrict__ out_off, uint8_t* __rest
         const uint64_t g = off + r;
         uint64_t* dst = reinterpret_cast<uint64_t*>(out_rec + g * W);
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxW / 8; ++k)
-          if (k < KW) dst[k] = k < Ks[u] ? bswap64(w[u][k]) : 0ull;
+        for (uint32_t k = 0; k < KW; ++k) dst[k] = k < Ks[u] ? bswap64(w[u][k]) : 0ull;
         out_perm[g] = pm[u];
       }
     }
     __syncthreads();
   }
+}
+
+// The gather with as many CTAs as fit the SMs (its register count falls with
+// the record width).
+template <int KW>
+cudaError_t launch_gather(int sms, const Many& m, uint32_t* out_off, uint8_t* out_rec, uint32_t* out_perm,
+                          cudaStream_t s) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, many_gather_kernel<KW>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  const uint32_t g = static_cast<uint32_t>(sms) * (occ < 1 ? 1u : occ > 8 ? 8u : static_cast<uint32_t>(occ));
+  BSORT_LAUNCH("many_gather", many_gather_kernel<KW>, g, kThreads, 0, s, m, out_off, out_rec, out_perm);
+  return cudaGetLastError();
 }
 
 __global__ void many_finish_kernel(Many m, int32_t* __restrict__ status) {
@@ -770,7 +785,13 @@ cudaError_t launch_many(const uint8_t* text_or_rec, const uint8_t* len, const bs
                  src);
     src ^= 1;
   }
-  BSORT_LAUNCH("many_gather", many_gather_kernel, grid, kThreads, 0, s, m, out_off, out_rec, out_perm);
+  switch (KW) {
+    case 1: e = launch_gather<1>(sms, m, out_off, out_rec, out_perm, s); break;
+    case 2: e = launch_gather<2>(sms, m, out_off, out_rec, out_perm, s); break;
+    case 3: e = launch_gather<3>(sms, m, out_off, out_rec, out_perm, s); break;
+    default: e = launch_gather<4>(sms, m, out_off, out_rec, out_perm, s); break;
+  }
+  if (e != cudaSuccess) return e;
   BSORT_LAUNCH("many_finish", many_finish_kernel, 16, 256, 0, s, m, list_status);
   return cudaGetLastError();
 }
