@@ -784,7 +784,8 @@ def run_variant(args):
     """The large table through the paper's other two forms: `whole` is the
     unbucketed order (Table 2, second row: every word by its bytes), `packed`
     the bucketed order written as packed bytes plus offsets (the "vectors of
-    string" of §3.1).  One step = one call of each form's path."""
+    string" of §3.1) by the sort's last kernel.  One step = one call of each
+    form's path."""
     import torch
 
     import paper_1411_5283_gb300 as bs
@@ -799,9 +800,10 @@ def run_variant(args):
         def step():
             s.sort_records_whole(rec, ln, n, alg=args.alg)
     else:
+        offsets = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+
         def step():
-            s.sort_records(rec, ln, n, alg=args.alg)
-            s.pack(n, bucketed=True, out_bytes=out_bytes)
+            s.sort_records_packed(rec, ln, n, alg=args.alg, out_bytes=out_bytes, offsets=offsets)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

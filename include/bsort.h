@@ -223,6 +223,35 @@ bsort_status bsort_pack_words(uint32_t n, uint32_t W, const uint8_t* d_rec, cons
                               uint64_t bytes_cap, uint32_t* d_offsets, void* d_ws,
                               size_t ws_bytes, cudaStream_t s);
 
+/* bsort_sort_records with the answer in the "vectors of string" form of §3.1
+ * instead of records: the sort's last kernel writes the sorted words (in the
+ * bucketed order of the other calls) back to back without padding into
+ * d_bytes, word r at d_bytes[d_offsets[r] .. d_offsets[r+1]-1], d_offsets[n] =
+ * total bytes, and the permutation to d_out_perm[n] and the bucket offsets to
+ * d_off as bsort_sort_records does; no fixed-width records are written.
+ * Same bytes and offsets as bsort_sort_records followed by bsort_pack_words
+ * with d_off.  bytes_cap is the capacity of d_bytes: a larger total records
+ * BSORT_E_CAPACITY in the workspace status, writes no bytes and sets
+ * d_offsets[n] = 0 (the other outputs are still written).  n must be at most
+ * 2^28 words and n W below 2^32 (else BSORT_E_CAPACITY before any work).
+ * d_bytes has no alignment requirement; d_rec as bsort_sort_records. */
+bsort_status bsort_sort_records_packed(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                       uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                       uint8_t* d_bytes, uint64_t bytes_cap, uint32_t* d_offsets,
+                                       uint32_t* d_out_perm, uint32_t* d_off, void* d_ws,
+                                       size_t ws_bytes, cudaStream_t s);
+
+/* bsort_sort_text with the packed answer of bsort_sort_records_packed
+ * (phases 1-3 of §3, output as in §3.1): n = the device-side word count
+ * *d_n_words, d_offsets[n] = total bytes; max_words bounds n for the 2^28 and
+ * 2^32 limits.  The tokenised records still go to d_rec / d_len / d_src_off. */
+bsort_status bsort_sort_text_packed(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                                    uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                                    uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                                    uint32_t* d_n_words, uint8_t* d_bytes, uint64_t bytes_cap,
+                                    uint32_t* d_offsets, uint32_t* d_out_perm, uint32_t* d_off,
+                                    void* d_ws, size_t ws_bytes, cudaStream_t s);
+
 /* The paper has no counterpart to this entry point.
  * bsort_sort_records without a workspace, for callers that may not allocate
  * device memory: code whose device memory belongs to a host framework's own

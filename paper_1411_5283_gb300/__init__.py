@@ -12,8 +12,9 @@ from ._lib import (ALGS, AUTO, MERGE, ODD_EVEN, BsortError, ListDesc, Tune,  # n
                    bsort_bucket_by_length, bsort_export_buckets, bsort_gather,
                    bsort_get_status, bsort_pack_words, bsort_profile_enable, bsort_profile_read,
                    bsort_profile_reset, bsort_reset_status, bsort_sort_buckets, bsort_sort_many,
-                   bsort_sort_many_workspace_size, bsort_sort_records, bsort_sort_records_whole,
-                   bsort_sort_text, bsort_sort_text_whole,
+                   bsort_sort_many_workspace_size, bsort_sort_records, bsort_sort_records_packed,
+                   bsort_sort_records_whole, bsort_sort_text, bsort_sort_text_packed,
+                   bsort_sort_text_whole,
                    bsort_status_string, bsort_tokenize, bsort_workspace_capacity, bsort_workspace_init,
                    bsort_workspace_size)
 
@@ -116,6 +117,38 @@ class Sorter:
                          None if bucketed else perm, None if bucketed else ln, out_bytes,
                          int(out_bytes.numel()), offsets, self.ws, self.ws_bytes)
         return out_bytes, offsets
+
+    def sort_records_packed(self, rec, ln, n: int | None = None, alg="auto", tune=None,
+                            out_bytes=None, offsets=None):
+        """Phases 2-3 with the answer packed without padding (§3.1) by the
+        sort's last kernel; returns (bytes, offsets[n + 1], out_perm, off).
+        The default byte buffer holds n W bytes."""
+        torch = self.torch
+        n = int(ln.numel()) if n is None else n
+        if out_bytes is None:
+            out_bytes = torch.empty(max(n * self.W, 16), dtype=torch.uint8, device=self.device)
+        if offsets is None:
+            offsets = torch.empty(n + 1, dtype=torch.int32, device=self.device)
+        bsort_sort_records_packed(rec, ln, n, self.W, alg, tune, out_bytes, int(out_bytes.numel()),
+                                  offsets, self.out_perm, self.off, self.ws, self.ws_bytes)
+        return out_bytes, offsets, self.out_perm[:n], self.off
+
+    def sort_text_packed(self, text, alg="auto", tune=None, max_words: int | None = None,
+                         out_bytes=None, offsets=None):
+        """Phases 1-3 on raw text with the packed answer; returns (bytes,
+        offsets, out_perm, off, n_words device tensor).  offsets[n_words] is
+        the total; entries past it are unspecified."""
+        torch = self.torch
+        mw = self.max_words if max_words is None else max_words
+        self._text_buffers(mw)
+        if out_bytes is None:
+            out_bytes = torch.empty(max(mw * self.W, 16), dtype=torch.uint8, device=self.device)
+        if offsets is None:
+            offsets = torch.empty(mw + 1, dtype=torch.int32, device=self.device)
+        bsort_sort_text_packed(text, text.numel(), self.W, mw, alg, tune, self.rec, self.len,
+                               self.src_off, self.n_words, out_bytes, int(out_bytes.numel()),
+                               offsets, self.out_perm, self.off, self.ws, self.ws_bytes)
+        return out_bytes, offsets, self.out_perm, self.off, self.n_words
 
     def _text_buffers(self, mw: int):
         torch = self.torch

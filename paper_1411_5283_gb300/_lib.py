@@ -70,6 +70,14 @@ _SIGS = {
     "bsort_pack_words": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, c_u8p, c_u8p, c_u8p,
                                         c_u8p, c_u8p, ctypes.c_uint64, c_u8p, c_u8p, c_size,
                                         c_u8p]),
+    "bsort_sort_records_packed": (ctypes.c_int, [c_u8p, c_u8p, ctypes.c_uint32, ctypes.c_uint32,
+                                                 ctypes.c_int, ctypes.POINTER(Tune), c_u8p,
+                                                 ctypes.c_uint64, c_u8p, c_u8p, c_u8p, c_u8p,
+                                                 c_size, c_u8p]),
+    "bsort_sort_text_packed": (ctypes.c_int, [c_u8p, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(Tune),
+                                              c_u8p, c_u8p, c_u8p, c_u8p, c_u8p, ctypes.c_uint64,
+                                              c_u8p, c_u8p, c_u8p, c_u8p, c_size, c_u8p]),
     "bsort_sort_records_noalloc": (ctypes.c_int, [c_u8p, c_u8p, ctypes.c_uint32, ctypes.c_uint32,
                                                   ctypes.c_int, ctypes.POINTER(Tune), c_u8p,
                                                   c_u8p, c_u8p, c_u8p, c_u8p]),
@@ -233,6 +241,24 @@ def bsort_pack_words(n, W, rec, off, perm, ln, out_bytes, bytes_cap, offsets, ws
     _check(load().bsort_pack_words(n, W, _ptr(rec), _ptr(off), _ptr(perm), _ptr(ln),
                                    _ptr(out_bytes), bytes_cap, _ptr(offsets), _ptr(ws), ws_bytes,
                                    _stream(stream)), "bsort_pack_words")
+
+
+def bsort_sort_records_packed(rec, ln, n, W, alg, tune, out_bytes, bytes_cap, offsets, out_perm,
+                              off, ws, ws_bytes, stream=None):
+    _check(load().bsort_sort_records_packed(_ptr(rec), _ptr(ln), n, W, _alg(alg), _tune(tune),
+                                            _ptr(out_bytes), bytes_cap, _ptr(offsets),
+                                            _ptr(out_perm), _ptr(off), _ptr(ws), ws_bytes,
+                                            _stream(stream)), "bsort_sort_records_packed")
+
+
+def bsort_sort_text_packed(text, n_bytes, W, max_words, alg, tune, rec, ln, src_off, n_words,
+                           out_bytes, bytes_cap, offsets, out_perm, off, ws, ws_bytes,
+                           stream=None):
+    _check(load().bsort_sort_text_packed(_ptr(text), n_bytes, W, max_words, _alg(alg),
+                                         _tune(tune), _ptr(rec), _ptr(ln), _ptr(src_off),
+                                         _ptr(n_words), _ptr(out_bytes), bytes_cap,
+                                         _ptr(offsets), _ptr(out_perm), _ptr(off), _ptr(ws),
+                                         ws_bytes, _stream(stream)), "bsort_sort_text_packed")
 
 
 def bsort_sort_many_workspace_size(total_words: int, n_lists: int, W: int) -> int:

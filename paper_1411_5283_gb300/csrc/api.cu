@@ -213,14 +213,15 @@ bsort_status bsort_gather(uint32_t n, uint32_t W, const uint32_t* d_off, const v
 namespace {
 
 // The one-call paths, with the bucket offsets at d_off; whole = true adds the
-// merge of the buckets into the unbucketed order.
+// merge of the buckets into the unbucketed order.  With pk the final write
+// packs the words (bucketed order only; d_out_rec is then unused).
 bsort_status sort_records_impl(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n, uint32_t W,
                                bsort_alg alg, const bsort_tune* tune, uint8_t* d_out_rec,
                                uint32_t* d_out_perm, uint32_t* d_off, void* d_ws, size_t ws_bytes,
-                               bool whole, cudaStream_t s) {
+                               bool whole, cudaStream_t s, const PackOut* pk = nullptr) {
   if (!valid_W(W) || !d_off || n > 0xFFFFFFFEu) return BSORT_E_INVALID;
-  if (n && (!d_rec || !d_len || !d_out_rec || !d_out_perm)) return BSORT_E_INVALID;
-  if (n && (!aligned(d_rec, 16) || !aligned(d_out_rec, 16))) return BSORT_E_INVALID;
+  if (n && (!d_rec || !d_len || (!pk && !d_out_rec) || !d_out_perm)) return BSORT_E_INVALID;
+  if (n && (!aligned(d_rec, 16) || (!pk && !aligned(d_out_rec, 16)))) return BSORT_E_INVALID;
   if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
   SortParams p;
   if (!resolve(alg, tune, W, &p)) return BSORT_E_INVALID;
@@ -229,11 +230,11 @@ bsort_status sort_records_impl(const uint8_t* d_rec, const uint8_t* d_len, uint3
   if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BSORT_E_CUDA;
   cudaError_t e;
   if (alg == BSORT_AUTO && auto_applies(n, ws, W)) {
-    e = launch_auto(d_rec, d_len, n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
+    e = launch_auto(d_rec, d_len, n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s, pk);
   } else {
     e = launch_bucket(d_rec, d_len, n, nullptr, W, d_off, ws, s);
     if (e == cudaSuccess) e = launch_sort(n, W, p, d_off, ws, s);
-    if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s);
+    if (e == cudaSuccess) e = launch_gather(n, nullptr, W, d_off, ws, d_out_rec, d_out_perm, s, pk);
   }
   if (e == cudaSuccess && whole) e = launch_whole(n, W, d_off, ws, d_out_rec, d_out_perm, s);
   return cuda_status(e);
@@ -243,13 +244,13 @@ bsort_status sort_text_impl(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
                             bsort_alg alg, const bsort_tune* tune, uint8_t* d_rec, uint8_t* d_len,
                             uint32_t* d_src_off, uint32_t* d_n_words, uint8_t* d_out_rec,
                             uint32_t* d_out_perm, uint32_t* d_off, void* d_ws, size_t ws_bytes,
-                            bool whole, cudaStream_t s) {
+                            bool whole, cudaStream_t s, const PackOut* pk = nullptr) {
   if (!valid_W(W) || n_bytes > 0xFFFF0000ull || (n_bytes && !d_text) || !d_off || !d_n_words)
     return BSORT_E_INVALID;
   if (max_words > 0xFFFFFFFEu) return BSORT_E_INVALID;
-  if (max_words && (!d_rec || !d_len || !d_src_off || !d_out_rec || !d_out_perm))
+  if (max_words && (!d_rec || !d_len || !d_src_off || (!pk && !d_out_rec) || !d_out_perm))
     return BSORT_E_INVALID;
-  if (max_words && (!aligned(d_rec, 16) || !aligned(d_out_rec, 16))) return BSORT_E_INVALID;
+  if (max_words && (!aligned(d_rec, 16) || (!pk && !aligned(d_out_rec, 16)))) return BSORT_E_INVALID;
   if (alg != BSORT_ODD_EVEN && alg != BSORT_MERGE && alg != BSORT_AUTO) return BSORT_E_INVALID;
   SortParams p;
   if (!resolve(alg, tune, W, &p)) return BSORT_E_INVALID;
@@ -259,12 +260,12 @@ bsort_status sort_text_impl(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
   cudaError_t e = launch_tokenize(d_text, static_cast<uint32_t>(n_bytes), W, max_words, d_rec,
                                   d_len, d_src_off, d_n_words, ws, s);
   if (e == cudaSuccess && alg == BSORT_AUTO && auto_applies(max_words, ws, W)) {
-    e = launch_auto(d_rec, d_len, max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
+    e = launch_auto(d_rec, d_len, max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s, pk);
   } else {
     if (e == cudaSuccess) e = launch_bucket(d_rec, d_len, max_words, d_n_words, W, d_off, ws, s);
     if (e == cudaSuccess) e = launch_sort(max_words, W, p, d_off, ws, s);
     if (e == cudaSuccess)
-      e = launch_gather(max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s);
+      e = launch_gather(max_words, d_n_words, W, d_off, ws, d_out_rec, d_out_perm, s, pk);
   }
   if (e == cudaSuccess && whole) e = launch_whole(max_words, W, d_off, ws, d_out_rec, d_out_perm, s);
   return cuda_status(e);
@@ -274,6 +275,17 @@ bsort_status sort_text_impl(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
 uint32_t* internal_off(void* d_ws, size_t ws_bytes, uint32_t W) {
   if (!valid_W(W) || !d_ws || !aligned(d_ws, 256)) return nullptr;
   return ws_view(d_ws, ws_bytes, W).misc;
+}
+
+// Arguments of the packed calls: n words at most (n_max), bytes[cap].
+bsort_status packed_args(uint32_t n_max, uint32_t W, uint8_t* d_bytes, uint64_t bytes_cap,
+                         uint32_t* d_offsets, PackOut* pk) {
+  if (!valid_W(W) || !d_offsets) return BSORT_E_INVALID;
+  if (n_max > pack_max_words() || static_cast<uint64_t>(n_max) * W > 0xFFFFFFFFull)
+    return BSORT_E_CAPACITY;
+  if (n_max && !d_bytes) return BSORT_E_INVALID;
+  *pk = PackOut{d_bytes, d_offsets, bytes_cap};
+  return BSORT_OK;
 }
 
 }  // namespace
@@ -316,6 +328,29 @@ bsort_status bsort_sort_text_whole(const uint8_t* d_text, uint64_t n_bytes, uint
   if (!off) return valid_W(W) ? BSORT_E_WORKSPACE : BSORT_E_INVALID;
   return sort_text_impl(d_text, n_bytes, W, max_words, alg, tune, d_rec, d_len, d_src_off,
                         d_n_words, d_out_rec, d_out_perm, off, d_ws, ws_bytes, true, s);
+}
+
+bsort_status bsort_sort_records_packed(const uint8_t* d_rec, const uint8_t* d_len, uint32_t n,
+                                       uint32_t W, bsort_alg alg, const bsort_tune* tune,
+                                       uint8_t* d_bytes, uint64_t bytes_cap, uint32_t* d_offsets,
+                                       uint32_t* d_out_perm, uint32_t* d_off, void* d_ws,
+                                       size_t ws_bytes, cudaStream_t s) {
+  PackOut pk;
+  if (const bsort_status e = packed_args(n, W, d_bytes, bytes_cap, d_offsets, &pk)) return e;
+  return sort_records_impl(d_rec, d_len, n, W, alg, tune, nullptr, d_out_perm, d_off, d_ws,
+                           ws_bytes, false, s, &pk);
+}
+
+bsort_status bsort_sort_text_packed(const uint8_t* d_text, uint64_t n_bytes, uint32_t W,
+                                    uint32_t max_words, bsort_alg alg, const bsort_tune* tune,
+                                    uint8_t* d_rec, uint8_t* d_len, uint32_t* d_src_off,
+                                    uint32_t* d_n_words, uint8_t* d_bytes, uint64_t bytes_cap,
+                                    uint32_t* d_offsets, uint32_t* d_out_perm, uint32_t* d_off,
+                                    void* d_ws, size_t ws_bytes, cudaStream_t s) {
+  PackOut pk;
+  if (const bsort_status e = packed_args(max_words, W, d_bytes, bytes_cap, d_offsets, &pk)) return e;
+  return sort_text_impl(d_text, n_bytes, W, max_words, alg, tune, d_rec, d_len, d_src_off,
+                        d_n_words, nullptr, d_out_perm, d_off, d_ws, ws_bytes, false, s, &pk);
 }
 
 bsort_status bsort_pack_words(uint32_t n, uint32_t W, const uint8_t* d_rec, const uint32_t* d_off,

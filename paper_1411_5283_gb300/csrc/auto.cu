@@ -1125,29 +1125,51 @@ constexpr size_t kSegPlanesBytes = 106624;
 constexpr size_t kSegBufBytes = 16 + kSegPlanesBytes;
 __host__ __device__ constexpr size_t segsort_smem_bytes() { return kSegBufBytes; }
 
-template <int K>
-__device__ __forceinline__ void write_word(uint32_t W, uint8_t* out_rec, uint32_t* out_perm,
-                                           uint32_t r, const Elem<K>& e) {
-  const uint32_t KW = W / 8;
-  uint64_t* dst = reinterpret_cast<uint64_t*>(out_rec + static_cast<uint64_t>(r) * W);
-  if ((W & 15u) == 0) {
-    for (uint32_t k = 0; k < KW; k += 2) {
-      const uint64_t a = k < static_cast<uint32_t>(K) ? bswap64(e.k[k]) : 0ull;
-      const uint64_t b = k + 1 < static_cast<uint32_t>(K) ? bswap64(e.k[k + 1]) : 0ull;
-      reinterpret_cast<ulonglong2*>(dst)[k / 2] = make_ulonglong2(a, b);
+// Where the segment sort puts the word of output rank r: its input index to
+// perm[r] and either the zero-padded record at rec[r W] (RecSink) or, in the
+// packed form (§3.1), its L bytes at bytes[base + r L] with that start in
+// offsets[r] (PackSink; the bytes only when the total fits the buffer).
+struct RecSink {
+  uint8_t* rec;
+  uint32_t* perm;
+  uint32_t W;
+  template <int K>
+  __device__ __forceinline__ void put(uint32_t r, const Elem<K>& e) const {
+    const uint32_t KW = W / 8;
+    uint64_t* dst = reinterpret_cast<uint64_t*>(rec + static_cast<uint64_t>(r) * W);
+    if ((W & 15u) == 0) {
+      for (uint32_t k = 0; k < KW; k += 2) {
+        const uint64_t a = k < static_cast<uint32_t>(K) ? bswap64(e.k[k]) : 0ull;
+        const uint64_t b = k + 1 < static_cast<uint32_t>(K) ? bswap64(e.k[k + 1]) : 0ull;
+        reinterpret_cast<ulonglong2*>(dst)[k / 2] = make_ulonglong2(a, b);
+      }
+    } else {
+      for (uint32_t k = 0; k < KW; ++k) dst[k] = k < static_cast<uint32_t>(K) ? bswap64(e.k[k]) : 0ull;
     }
-  } else {
-    for (uint32_t k = 0; k < KW; ++k) dst[k] = k < static_cast<uint32_t>(K) ? bswap64(e.k[k]) : 0ull;
+    perm[r] = e.idx;
   }
-  out_perm[r] = e.idx;
-}
+};
+
+struct PackSink {
+  uint8_t* bytes;
+  uint32_t* offsets;
+  uint32_t* perm;
+  uint32_t L, base, fits;
+  template <int K>
+  __device__ __forceinline__ void put(uint32_t r, const Elem<K>& e) const {
+    const uint32_t o = base + r * L;
+    offsets[r] = o;
+    if (fits) put_word_bytes<K>(bytes + o, L, e.k);
+    perm[r] = e.idx;
+  }
+};
 
 // A segment larger than shared memory (only after a retry, whose region is
 // data + scratch): sort chunks in shared memory, then merge runs pairwise with
 // merge-path tiles, ping-ponging between the two halves.
-template <int K>
+template <int K, typename Sink>
 __device__ void segsort_big(uint8_t* smem, const AutoView& v, uint32_t seg, uint32_t c,
-                            uint32_t W, uint8_t* out_rec, uint32_t* out_perm) {
+                            const Sink& o) {
   const uint32_t rc = v.rcap[seg], half = rc / 2;
   const uint64_t rb = v.rbase[seg], ib = v.ibase[seg];
   SmemTile<K> a, b, t;
@@ -1181,8 +1203,7 @@ __device__ void segsort_big(uint8_t* smem, const AutoView& v, uint32_t seg, uint
     dst = x;
   }
   const uint32_t ob = v.outbase[seg];
-  for (uint32_t r = threadIdx.x; r < c; r += blockDim.x)
-    write_word<K>(W, out_rec, out_perm, ob + r, src.get(r));
+  for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) o.template put<K>(ob + r, src.get(r));
   __syncthreads();
 }
 
@@ -1774,8 +1795,9 @@ __device__ __noinline__ uint32_t k1_radix(uint32_t buf_off, uint32_t c, ByteCode
 // Output records and permutation of a sorted one-key segment: codes (with the
 // index in their low ib bits when idx_off is 0, else in the plane at idx_off)
 // in the key plane at buf_off.
+template <typename Sink>
 __device__ __noinline__ void k1_write(uint32_t buf_off, uint32_t idx_off, uint32_t c, ByteCode bc, uint32_t ib,
-                                      uint32_t W, uint32_t ob, uint8_t* out_rec, uint32_t* out_perm) {
+                                      uint32_t ob, Sink o) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint64_t* kp = reinterpret_cast<const uint64_t*>(smem_raw + buf_off);
   if (idx_off == 0) {
@@ -1785,7 +1807,7 @@ __device__ __noinline__ void k1_write(uint32_t buf_off, uint32_t idx_off, uint32
       Elem<1> e;
       e.k[0] = bc.decode(v >> ib);
       e.idx = static_cast<uint32_t>(v & imask);
-      write_word<1>(W, out_rec, out_perm, ob + r, e);
+      o.template put<1>(ob + r, e);
     }
   } else {
     const uint32_t* op = reinterpret_cast<const uint32_t*>(smem_raw + idx_off);
@@ -1793,7 +1815,7 @@ __device__ __noinline__ void k1_write(uint32_t buf_off, uint32_t idx_off, uint32
       Elem<1> e;
       e.k[0] = bc.decode(kp[r]);
       e.idx = op[r];
-      write_word<1>(W, out_rec, out_perm, ob + r, e);
+      o.template put<1>(ob + r, e);
     }
   }
   __syncthreads();
@@ -1804,9 +1826,9 @@ __device__ __noinline__ void k1_write(uint32_t buf_off, uint32_t idx_off, uint32
 // bitonic network in shared memory, which keeps no elements in registers.
 // (A register network over (first key word, slot) pairs was measured slower
 // for these segments.)
-template <int K>
+template <int K, typename Sink>
 __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uint32_t c,
-                              uint32_t W, uint8_t* out_rec, uint32_t* out_perm) {
+                              const Sink& o) {
   uint64_t* kp = reinterpret_cast<uint64_t*>(buf + 16);
   const uint32_t C = static_cast<uint32_t>(seg_plane_elems(K));
   SmemTile<K> t;
@@ -1816,7 +1838,7 @@ __device__ void sort_resident(uint8_t* buf, const AutoView& v, uint32_t seg, uin
   bitonic_flip<K>(t, c);
   __syncthreads();
   const uint32_t ob = v.outbase[seg];
-  for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) write_word<K>(W, out_rec, out_perm, ob + r, t.get(r));
+  for (uint32_t r = threadIdx.x; r < c; r += blockDim.x) o.template put<K>(ob + r, t.get(r));
   __syncthreads();
 }
 
@@ -1875,9 +1897,9 @@ __device__ __noinline__ uint32_t k2_radix(uint32_t buf_off, uint32_t c, const ui
 }
 
 // Output records and permutation of a sorted two-key segment (as k1_write).
+template <typename Sink>
 __device__ __noinline__ void k2_write(uint32_t buf_off, uint32_t idx_off, uint32_t c, const uint32_t* f,
-                                      uint32_t ib, uint32_t W, uint32_t ob, uint8_t* out_rec,
-                                      uint32_t* out_perm) {
+                                      uint32_t ib, uint32_t ob, Sink o) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint64_t* k0p = reinterpret_cast<const uint64_t*>(smem_raw + buf_off);
   if (idx_off == 0) {
@@ -1887,7 +1909,7 @@ __device__ __noinline__ void k2_write(uint32_t buf_off, uint32_t idx_off, uint32
       Elem<2> e;
       decode16(f, v >> ib, e);
       e.idx = static_cast<uint32_t>(v & imask);
-      write_word<2>(W, out_rec, out_perm, ob + r, e);
+      o.template put<2>(ob + r, e);
     }
   } else {
     const uint32_t* op = reinterpret_cast<const uint32_t*>(smem_raw + idx_off);
@@ -1895,7 +1917,7 @@ __device__ __noinline__ void k2_write(uint32_t buf_off, uint32_t idx_off, uint32
       Elem<2> e;
       decode16(f, k0p[r], e);
       e.idx = op[r];
-      write_word<2>(W, out_rec, out_perm, ob + r, e);
+      o.template put<2>(ob + r, e);
     }
   }
   __syncthreads();
@@ -1904,9 +1926,9 @@ __device__ __noinline__ void k2_write(uint32_t buf_off, uint32_t idx_off, uint32
 // Two-key segment resident in buf: a code (from the segment's record) of at
 // most 64 bits takes the item sort, a wider one the bitonic network.  Returns
 // false when the code is too wide.
+template <typename Sink>
 __device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
-                                 uint32_t seg, uint32_t c, uint32_t W, uint8_t* out_rec,
-                                 uint32_t* out_perm) {
+                                 uint32_t seg, uint32_t c, const Sink& o) {
   __shared__ uint32_t s_f2[16], s_kb2, s_ib2;
   const uint32_t* sf = v.segf + static_cast<size_t>(seg) * kSegFWords;
   if (threadIdx.x < 16) s_f2[threadIdx.x] = __ldg(sf + threadIdx.x);
@@ -1925,15 +1947,15 @@ __device__ bool sort_resident_k2(const uint8_t* smem_base, uint8_t* buf, const A
     if (c <= 4 * kSegThreads) idx_off = k2_radix<Item96, 4>(off, c, s_f2, kb, ib);
     else idx_off = k2_radix<Item96, 8>(off, c, s_f2, kb, ib);
   }
-  k2_write(off, idx_off, c, s_f2, ib, W, ob, out_rec, out_perm);
+  k2_write(off, idx_off, c, s_f2, ib, ob, o);
   return true;
 }
 
 // One-key segment resident in buf: its byte code (from the segment's record)
 // recodes the keys, then the (code, index) items are sorted.
+template <typename Sink>
 __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
-                                 uint32_t seg, uint32_t c, uint32_t W, uint8_t* out_rec,
-                                 uint32_t* out_perm) {
+                                 uint32_t seg, uint32_t c, const Sink& o) {
   const uint32_t* sf = v.segf + static_cast<size_t>(seg) * kSegFWords;
   ByteCode bc;
   bc.lo = (static_cast<uint64_t>(__ldg(sf + 18)) << 32) | __ldg(sf + 19);
@@ -1956,21 +1978,68 @@ __device__ void sort_resident_k1(const uint8_t* smem_base, uint8_t* buf, const A
     else if (c <= 8 * kSegThreads) idx_off = k1_radix<Item96, 8>(off, c, bc, kb, ib);
     else idx_off = k1_radix<Item96, 16>(off, c, bc, kb, ib);
   }
-  k1_write(off, idx_off, c, bc, ib, W, ob, out_rec, out_perm);
+  k1_write(off, idx_off, c, bc, ib, ob, o);
 }
 
+// A segment larger than shared memory (after a retry) and a resident one.
+template <typename Sink>
+__device__ __forceinline__ void sort_big(uint8_t* scratch, const AutoView& v, uint32_t seg, uint32_t c,
+                                         uint32_t K, const Sink& o) {
+  switch (K) {
+    case 1: segsort_big<1>(scratch, v, seg, c, o); break;
+    case 2: segsort_big<2>(scratch, v, seg, c, o); break;
+    case 3: segsort_big<3>(scratch, v, seg, c, o); break;
+    default: segsort_big<4>(scratch, v, seg, c, o); break;
+  }
+}
+
+template <typename Sink>
+__device__ __forceinline__ void sort_resident_any(const uint8_t* smem_base, uint8_t* buf, const AutoView& v,
+                                                  uint32_t seg, uint32_t c, uint32_t K, const Sink& o) {
+  switch (K) {
+    case 1: sort_resident_k1(smem_base, buf, v, seg, c, o); break;
+    case 2:
+      if (!sort_resident_k2(smem_base, buf, v, seg, c, o)) sort_resident<2>(buf, v, seg, c, o);
+      break;
+    case 3: sort_resident<3>(buf, v, seg, c, o); break;
+    default: sort_resident<4>(buf, v, seg, c, o); break;
+  }
+}
+
+// Destinations of the segment sort: records (rec) or the packed form (bytes,
+// offsets, cap, with the bucket offsets off); the permutation either way.
+struct SegOut {
+  uint8_t* rec;
+  uint32_t* perm;
+  uint8_t* bytes;
+  uint32_t* offsets;
+  uint64_t cap;
+  const uint32_t* off;
+};
+
 // Persistent CTAs (two per SM) walk the segments: bulk-copy the segment into
-// shared memory, sort, write the output records and permutation.
+// shared memory, sort, write the output records (or packed words) and the
+// permutation.
+template <bool kPacked>
 __global__ void __launch_bounds__(kSegThreads, 2)
-auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_rec,
-                    uint32_t* __restrict__ out_perm) {
+auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, SegOut out) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* buf = smem_raw;  // 16-byte aligned: barrier, then the planes
   uint64_t* bar = reinterpret_cast<uint64_t*>(buf);
   const AutoView& v = av;  // kernel parameter: read from the constant bank
+  __shared__ uint32_t s_base[kPacked ? kMaxW + 2 : 1];
+  __shared__ uint32_t s_fits;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
+    if constexpr (kPacked) {
+      const uint32_t total = packed_bases(out.off, W, s_base);
+      s_fits = total <= out.cap;
+      if (blockIdx.x == 0) {
+        out.offsets[out.off[W + 1]] = s_fits ? total : 0u;
+        if (!s_fits) set_error(ws.hdr, BSORT_E_CAPACITY);
+      }
+    }
   }
   __syncthreads();
   const uint32_t G = v.hdr->G;
@@ -1991,13 +2060,10 @@ auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_re
     if (c == 0) continue;
     if (c > auto_seg_cap(K)) {
       // larger than shared memory (after a retry): chunked sort + merges
-      uint8_t* scratch = buf + 16;
-      switch (K) {
-        case 1: segsort_big<1>(scratch, v, seg, c, W, out_rec, out_perm); break;
-        case 2: segsort_big<2>(scratch, v, seg, c, W, out_rec, out_perm); break;
-        case 3: segsort_big<3>(scratch, v, seg, c, W, out_rec, out_perm); break;
-        default: segsort_big<4>(scratch, v, seg, c, W, out_rec, out_perm); break;
-      }
+      if constexpr (kPacked)
+        sort_big(buf + 16, v, seg, c, K, PackSink{out.bytes, out.offsets, out.perm, L, s_base[L], s_fits});
+      else
+        sort_big(buf + 16, v, seg, c, K, RecSink{out.rec, out.perm, W});
       continue;
     }
     // earlier generic-proxy use of the buffer must be ordered before the bulk
@@ -2014,15 +2080,11 @@ auto_segsort_kernel(uint32_t W, Ws ws, AutoView av, uint8_t* __restrict__ out_re
       }
       return;
     }
-    switch (K) {
-      case 1: sort_resident_k1(smem_raw, buf, v, seg, c, W, out_rec, out_perm); break;
-      case 2:
-        if (!sort_resident_k2(smem_raw, buf, v, seg, c, W, out_rec, out_perm))
-          sort_resident<2>(buf, v, seg, c, W, out_rec, out_perm);
-        break;
-      case 3: sort_resident<3>(buf, v, seg, c, W, out_rec, out_perm); break;
-      default: sort_resident<4>(buf, v, seg, c, W, out_rec, out_perm); break;
-    }
+    if constexpr (kPacked)
+      sort_resident_any(smem_raw, buf, v, seg, c, K,
+                        PackSink{out.bytes, out.offsets, out.perm, L, s_base[L], s_fits});
+    else
+      sort_resident_any(smem_raw, buf, v, seg, c, K, RecSink{out.rec, out.perm, W});
   }
 }
 
@@ -2168,11 +2230,13 @@ bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W) {
 
 cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
-                        uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {
-  static SmemOptIn split_set, select_set, seg_set;
+                        uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s, const PackOut* pk) {
+  static SmemOptIn split_set, select_set, seg_set, seg_packed_set;
   cudaError_t e = ensure_smem(auto_spl_sort_kernel, kSplSortSmem, &split_set);
   if (e == cudaSuccess) e = ensure_smem(auto_spl_select_kernel, kSplSelectSmem, &select_set);
-  if (e == cudaSuccess) e = ensure_smem(auto_segsort_kernel, segsort_smem_bytes(), &seg_set);
+  if (e == cudaSuccess && !pk) e = ensure_smem(auto_segsort_kernel<false>, segsort_smem_bytes(), &seg_set);
+  if (e == cudaSuccess && pk)
+    e = ensure_smem(auto_segsort_kernel<true>, segsort_smem_bytes(), &seg_packed_set);
   if (e != cudaSuccess) return e;
   const int sms = device_sm_count();
   const uint32_t samples = n_cap / kAutoSampleEvery + 1;
@@ -2219,8 +2283,15 @@ cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = partition(W, d_off, ws, v, 1, s);
   if (e != cudaSuccess) return e;
-  BSORT_LAUNCH("auto_segsort", auto_segsort_kernel, static_cast<uint32_t>(sms) * 2,
-               kSegThreads, segsort_smem_bytes(), s, W, ws, v, out_rec, out_perm);
+  const SegOut out{out_rec, out_perm, pk ? pk->bytes : nullptr, pk ? pk->offsets : nullptr,
+                   pk ? pk->cap : 0, d_off};
+  if (pk) {
+    BSORT_LAUNCH("auto_segsort_packed", auto_segsort_kernel<true>, static_cast<uint32_t>(sms) * 2,
+                 kSegThreads, segsort_smem_bytes(), s, W, ws, v, out);
+  } else {
+    BSORT_LAUNCH("auto_segsort", auto_segsort_kernel<false>, static_cast<uint32_t>(sms) * 2,
+                 kSegThreads, segsort_smem_bytes(), s, W, ws, v, out);
+  }
   return cudaGetLastError();
 }
 

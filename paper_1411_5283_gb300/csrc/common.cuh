@@ -291,6 +291,34 @@ __device__ __forceinline__ bool elem_less(const Elem<K>& a, const Elem<K>& b) {
   return a.idx < b.idx;
 }
 
+// Packed output of the bucketed order (§3.1, "vectors of string"): every word
+// of bucket L is L bytes long, so word r of bucket L starts at byte
+// P_L + (r - off[L]) L, P_L being the bytes of all shorter words.  Writes
+// base[L] = P_L - off[L] L (mod 2^32) for L = 1..W, so that the start is
+// base[L] + r L, and base[W + 1] = the total, which it returns.  With
+// n W < 2^32 every start and the total fit 32 bits.  One thread.
+__device__ __forceinline__ uint32_t packed_bases(const uint32_t* off, uint32_t W, uint32_t* base) {
+  uint32_t p = 0;
+  for (uint32_t L = 1; L <= W; ++L) {
+    const uint32_t lo = off[L], hi = off[L + 1];
+    base[L] = p - lo * L;
+    p += (hi - lo) * L;
+  }
+  base[W + 1] = p;
+  return p;
+}
+
+// The L bytes of a word (key words k[0..K-1], big-endian, K = ceil(L / 8)) to
+// dst, any alignment.
+template <int K>
+__device__ __forceinline__ void put_word_bytes(uint8_t* dst, uint32_t L, const uint64_t (&k)[K]) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const uint32_t m = min(8u, L - 8u * q);
+    for (uint32_t j = 0; j < m; ++j) dst[8 * q + j] = static_cast<uint8_t>(k[q] >> (56 - 8 * j));
+  }
+}
+
 // Shared-memory structure-of-arrays tile: planes of keys then idx.
 template <int K>
 struct SmemTile {

@@ -5,6 +5,8 @@
 // output rank r reads its keys at position r of the buffer that holds bucket
 // L's final run.  The record is rebuilt from the big-endian keys (bytes past
 // the word are zero in the keys), so the input records are not read again.
+// The packed form (§3.1, "vectors of string") writes the word's L bytes at
+// its offset instead of the record.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -25,11 +27,15 @@ __device__ __forceinline__ uint32_t bucket_of(const uint32_t* s_off, uint32_t W,
   return lo;
 }
 
+template <bool kPacked>
 __global__ void __launch_bounds__(kThreads)
 gather_kernel(const uint32_t* __restrict__ d_off, uint32_t n_cap, const uint32_t* __restrict__ d_n,
-              uint32_t W, Ws ws, uint8_t* __restrict__ out_rec, uint32_t* __restrict__ out_perm) {
+              uint32_t W, Ws ws, uint8_t* __restrict__ out_rec, uint32_t* __restrict__ out_perm,
+              PackOut pk) {
   __shared__ uint32_t s_off[kMaxW + 2];
   __shared__ uint32_t s_buf[kMaxW + 2];
+  __shared__ uint32_t s_base[kMaxW + 2];
+  __shared__ bool s_fits;
   if (threadIdx.x < W + 2) {
     s_off[threadIdx.x] = d_off[threadIdx.x];
     s_buf[threadIdx.x] = ws.hdr->final_buf[threadIdx.x];
@@ -37,10 +43,35 @@ gather_kernel(const uint32_t* __restrict__ d_off, uint32_t n_cap, const uint32_t
   __syncthreads();
   const uint32_t n = min(s_off[W + 1], d_n ? min(*d_n, n_cap) : n_cap);
   const uint32_t KW = W / 8;
+  if constexpr (kPacked) {
+    if (threadIdx.x == 0) {
+      const uint32_t total = packed_bases(s_off, W, s_base);
+      s_fits = total <= pk.cap;
+      if (blockIdx.x == 0) {
+        pk.offsets[n] = s_fits ? total : 0u;
+        if (!s_fits) set_error(ws.hdr, BSORT_E_CAPACITY);
+      }
+    }
+    __syncthreads();
+  }
   for (uint32_t r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
     const uint32_t L = bucket_of(s_off, W, r);
     const uint32_t K = keys_for_len(L);
     const int buf = static_cast<int>(s_buf[L]);
+    if constexpr (kPacked) {
+      const uint32_t o = s_base[L] + r * L;
+      pk.offsets[r] = o;
+      if (s_fits) {
+        for (uint32_t q = 0; q < K; ++q) {
+          const uint64_t key = ws.keys[buf][q * ws.cap + r];
+          const uint32_t m = min(8u, L - 8u * q);
+          for (uint32_t j = 0; j < m; ++j)
+            pk.bytes[o + 8 * q + j] = static_cast<uint8_t>(key >> (56 - 8 * j));
+        }
+      }
+      out_perm[r] = ws.idx[buf][r];
+      continue;
+    }
     uint64_t* dst = reinterpret_cast<uint64_t*>(out_rec + static_cast<uint64_t>(r) * W);
     for (uint32_t k = 0; k < KW; k += 2) {
       const uint64_t a = k < K ? bswap64(ws.keys[buf][k * ws.cap + r]) : 0ull;
@@ -93,9 +124,15 @@ uint32_t grid_for(uint32_t n) {
 }  // namespace
 
 cudaError_t launch_gather(uint32_t n_cap, const uint32_t* d_n, uint32_t W, const uint32_t* d_off,
-                          const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s) {
-  BSORT_LAUNCH("gather", gather_kernel, grid_for(n_cap), kThreads, 0, s, d_off, n_cap, d_n, W, ws,
-               out_rec, out_perm);
+                          const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s,
+                          const PackOut* pk) {
+  if (pk) {
+    BSORT_LAUNCH("gather_packed", gather_kernel<true>, grid_for(n_cap), kThreads, 0, s, d_off, n_cap,
+                 d_n, W, ws, out_rec, out_perm, *pk);
+  } else {
+    BSORT_LAUNCH("gather", gather_kernel<false>, grid_for(n_cap), kThreads, 0, s, d_off, n_cap, d_n,
+                 W, ws, out_rec, out_perm, PackOut{});
+  }
   return cudaGetLastError();
 }
 

@@ -54,13 +54,25 @@ cudaError_t launch_bucket(const uint8_t* rec, const uint8_t* len, uint32_t n_cap
 cudaError_t launch_hist(const uint8_t* len, uint32_t n_cap, const uint32_t* d_n, uint32_t W,
                         uint32_t* d_off, const Ws& ws, cudaStream_t s);
 
+// Packed destination of a bucketed call's final write (§3.1): the words back
+// to back in bytes[cap], offsets[n + 1].  A total above cap records
+// BSORT_E_CAPACITY, writes no bytes (the offsets still are) and sets
+// offsets[n] = 0.  The caller guarantees n W < 2^32.
+struct PackOut {
+  uint8_t* bytes;
+  uint32_t* offsets;
+  uint64_t cap;
+};
+
 // Sample-sort strategy (auto.cu): length totals and bucket offsets (d_off),
-// then the sort; writes the final records and permutation.  auto_applies()
-// says whether the sizes and the workspace suit it.
+// then the sort; writes the final records and permutation, or with pk the
+// packed words and the permutation (out_rec unused).  auto_applies() says
+// whether the sizes and the workspace suit it.
 bool auto_applies(uint32_t n_cap, const Ws& ws, uint32_t W);
 cudaError_t launch_auto(const uint8_t* rec, const uint8_t* len, uint32_t n_cap,
                         const uint32_t* d_n, uint32_t W, uint32_t* d_off, const Ws& ws,
-                        uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
+                        uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s,
+                        const PackOut* pk = nullptr);
 
 struct SortParams {
   int alg;             // bsort_alg (resolved: ODD_EVEN or MERGE)
@@ -82,9 +94,11 @@ bool resolve_params(bsort_alg alg, const bsort_tune* tune, uint32_t W, SortParam
 cudaError_t launch_sort(uint32_t n_cap, uint32_t W, const SortParams& p, const uint32_t* d_off,
                         const Ws& ws, cudaStream_t s);
 
-// Concatenation: sorted records (from the keys) and the permutation.
+// Concatenation: sorted records (from the keys) and the permutation, or with
+// pk the packed words and the permutation (out_rec unused).
 cudaError_t launch_gather(uint32_t n_cap, const uint32_t* d_n, uint32_t W, const uint32_t* d_off,
-                          const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s);
+                          const Ws& ws, uint8_t* out_rec, uint32_t* out_perm, cudaStream_t s,
+                          const PackOut* pk = nullptr);
 
 // Unbucketed order (whole.cu): merges the length buckets of a bucketed answer
 // in out_rec / out_perm (offsets d_off) into one run ordered by bytes, a

@@ -69,11 +69,14 @@ class HostPipeline:
         if "bytes" not in s:
             s["bytes"] = torch.empty(max(self.max_words * self.W, 16), dtype=torch.uint8,
                                      device=s["rec"].device)
+            s["offsets"] = torch.empty(self.max_words + 1, dtype=torch.int32,
+                                       device=s["rec"].device)
         with torch.cuda.stream(s["stream"]):
             s["rec"][:n].copy_(rec_h[:n], non_blocking=True)
             s["len"][:n].copy_(len_h[:n], non_blocking=True)
-            out_rec, out_perm, off = s["sorter"].sort_records(s["rec"], s["len"], n, alg=alg, tune=tune)
-            b, offsets = s["sorter"].pack(n, bucketed=True, out_bytes=s["bytes"])
+            b, offsets, out_perm, _ = s["sorter"].sort_records_packed(
+                s["rec"], s["len"], n, alg=alg, tune=tune, out_bytes=s["bytes"],
+                offsets=s["offsets"][:n + 1])
             bytes_h[:total_bytes].copy_(b[:total_bytes], non_blocking=True)
             offsets_h[:n + 1].copy_(offsets, non_blocking=True)
             out_perm_h[:n].copy_(out_perm, non_blocking=True)
