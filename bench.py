@@ -40,18 +40,18 @@ NCU_TRAFFIC = {
     # dram__bytes_read + dram__bytes_write of one launch on the 4,194,304-word
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
-    "auto_segsort": {"bytes": 4 * (60.66e6 + 126.03e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8db6b9708923",
-                                 "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
+    "auto_segsort": {"bytes": 4 * (60.71e6 + 126.42e6),
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "9d6e41f4f494",
+                                 "paper_1411_5283_gb300/csrc/common.cuh": "401ac195dfb3",
                                  "paper_1411_5283_gb300/csrc/sort_impl.cuh": "8244b70a0067",
                                  "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
-    "auto_partition": {"bytes": 4 * (55.21e6 + 2.62e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8db6b9708923",
-                                   "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
+    "auto_partition": {"bytes": 4 * (55.05e6 + 2.42e6),
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "9d6e41f4f494",
+                                   "paper_1411_5283_gb300/csrc/common.cuh": "401ac195dfb3",
                                    "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
-    "auto_bucket": {"bytes": 4 * (138.92e6 + 23.61e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "8db6b9708923",
-                                "paper_1411_5283_gb300/csrc/common.cuh": "5c3f6dca058d",
+    "auto_bucket": {"bytes": 4 * (138.86e6 + 23.33e6),
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "9d6e41f4f494",
+                                "paper_1411_5283_gb300/csrc/common.cuh": "401ac195dfb3",
                                 "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
 }
 
@@ -87,6 +87,9 @@ def parse():
                          "server; text: the 240,000-word raw text end to end; whole: the "
                          "unbucketed order of the large table; packed: the large table's answer "
                          "as packed bytes plus offsets")
+    ap.add_argument("--pack-form", choices=["one-call", "two-call"], default="one-call",
+                    help="packed: the sort writes the packed answer itself (one call), or "
+                         "writes records that bsort_pack_words then packs (two calls)")
     ap.add_argument("--lists", type=int, default=4096)
     ap.add_argument("--served-check", choices=["inline", "replay"], default="replay",
                     help="served: compare every response with the oracle during the timed "
@@ -784,8 +787,8 @@ def run_variant(args):
     """The large table through the paper's other two forms: `whole` is the
     unbucketed order (Table 2, second row: every word by its bytes), `packed`
     the bucketed order written as packed bytes plus offsets (the "vectors of
-    string" of §3.1) by the sort's last kernel.  One step = one call of each
-    form's path."""
+    string" of §3.1) by the sort's last kernel (or, with --pack-form two-call,
+    records packed by a second call).  One step = one pass of the form's path."""
     import torch
 
     import paper_1411_5283_gb300 as bs
@@ -799,6 +802,10 @@ def run_variant(args):
     if args.workload == "whole":
         def step():
             s.sort_records_whole(rec, ln, n, alg=args.alg)
+    elif args.pack_form == "two-call":
+        def step():
+            s.sort_records(rec, ln, n, alg=args.alg)
+            s.pack(n, bucketed=True, out_bytes=out_bytes)
     else:
         offsets = torch.empty(n + 1, dtype=torch.int32, device="cuda")
 
@@ -831,7 +838,8 @@ def run_variant(args):
             "unit": "Mwords/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOAD}", "alg": args.alg},
+            "config": {"workload": f"{args.workload}: {WORKLOAD}", "alg": args.alg,
+                       **({"pack_form": args.pack_form} if args.workload == "packed" else {})},
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()}}
     if args.workload == "packed":
         line["packed_output_bytes_per_word"] = round((total_bytes + 4 * (n + 1) + 4 * n) / n, 2)
