@@ -7,8 +7,9 @@ against the oracle (records, permutation and bucket offsets, bit for bit).
   MERGE, against the bubble sort per length;
 * the benchmark's table itself: 16,777,216 pre-tokenised 32-byte records of
   seed 2, under AUTO (the benchmarked call) and MERGE, against the oracle's
-  stable-sort formulation; its first 65,536 words sorted alone against the
-  bubble sort;
+  stable-sort formulation, and in the one-call packed form against the
+  oracle's packing; its first 65,536 words sorted alone against the bubble
+  sort;
 * the 4,096-list batch (seeds 0..4,095, sizes log-uniform in 64..65,536),
   every list against the oracle;
 * served requests up to 1,048,576 words, pre-tokenised and raw text, every
@@ -98,6 +99,25 @@ def test_benchmark_table_matches_oracle(env, large, alg):
     torch.cuda.synchronize()
     assert s.status() == 0
     assert_same_answer(out_rec, out_perm, off, expect, n)
+
+
+def test_benchmark_table_packed_matches_oracle(env, large):
+    """The benchmark's table through the one-call packed form (§3.1): bytes,
+    offsets, permutation and bucket offsets against the oracle's packing of
+    the oracle's answer."""
+    torch, bs, orc = env
+    rec, ln, expect = large
+    n = ln.size
+    want_bytes, want_off = orc.pack_words(expect.out_rec, ln[expect.out_perm])
+    s = bs.Sorter(n, 32)
+    b, offsets, perm, off = s.sort_records_packed(to_dev(rec, torch), to_dev(ln, torch), n,
+                                                  alg="auto")
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    assert np.array_equal(offsets.cpu().numpy().view(np.uint32), want_off)
+    assert np.array_equal(b[:int(want_off[-1])].cpu().numpy(), want_bytes)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), expect.out_perm)
+    assert np.array_equal(off.cpu().numpy().view(np.uint32), expect.off)
 
 
 def test_benchmark_table_prefix_matches_bubble_sort(env, large):
