@@ -83,3 +83,30 @@ def test_sort_many_workspace_size(lib):
     b = L.bsort_sort_many_workspace_size(1000, 10, 16)
     assert b > 0 and L.bsort_sort_many_workspace_size(1000, 10, 12) == 0
     assert L.bsort_sort_many_workspace_size(2000, 10, 16) > b
+
+
+def test_packed_calls_refuse_bad_sizes_before_any_work(lib):
+    """The packed calls check W, the offsets pointer and the 2^28-word /
+    2^32-byte limits on the host and return before touching the device (the
+    pointers below are never dereferenced)."""
+    L = lib.load()
+    fake = 1 << 20  # 16-byte aligned, never read
+    E_INVALID, E_CAPACITY = 1, 3
+    rec_call = L.bsort_sort_records_packed
+    # n W at 2^32 bytes, and n above 2^28 words
+    assert rec_call(fake, fake, 1 << 28, 16, 2, None, fake, 64, fake, fake, fake, fake, 1 << 20,
+                    None) == E_CAPACITY
+    assert rec_call(fake, fake, (1 << 28) + 1, 8, 2, None, fake, 64, fake, fake, fake, fake,
+                    1 << 20, None) == E_CAPACITY
+    # W not a multiple of 8, offsets missing, bytes missing for a non-empty call
+    assert rec_call(fake, fake, 10, 12, 2, None, fake, 64, fake, fake, fake, fake, 1 << 20,
+                    None) == E_INVALID
+    assert rec_call(fake, fake, 10, 16, 2, None, fake, 64, None, fake, fake, fake, 1 << 20,
+                    None) == E_INVALID
+    assert rec_call(fake, fake, 10, 16, 2, None, None, 64, fake, fake, fake, fake, 1 << 20,
+                    None) == E_INVALID
+    text_call = L.bsort_sort_text_packed
+    assert text_call(fake, 100, 16, 1 << 28, 2, None, fake, fake, fake, fake, fake, 64, fake, fake,
+                     fake, fake, 1 << 20, None) == E_CAPACITY
+    assert text_call(fake, 100, 16, 1000, 2, None, fake, fake, fake, fake, fake, 64, None, fake,
+                     fake, fake, 1 << 20, None) == E_INVALID
