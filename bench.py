@@ -41,16 +41,16 @@ NCU_TRAFFIC = {
     # cut of the table, x4 for 16,777,216 words; a lower bound: at 4M words
     # part of each kernel's output is still in L2 when the next one reads it
     "auto_segsort": {"bytes": 4 * (60.71e6 + 126.42e6),
-                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "9d6e41f4f494",
+                     "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "19ced58c997d",
                                  "paper_1411_5283_gb300/csrc/common.cuh": "401ac195dfb3",
                                  "paper_1411_5283_gb300/csrc/sort_impl.cuh": "8244b70a0067",
                                  "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
     "auto_partition": {"bytes": 4 * (55.05e6 + 2.42e6),
-                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "9d6e41f4f494",
+                       "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "19ced58c997d",
                                    "paper_1411_5283_gb300/csrc/common.cuh": "401ac195dfb3",
                                    "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
     "auto_bucket": {"bytes": 4 * (138.86e6 + 23.33e6),
-                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "9d6e41f4f494",
+                    "sources": {"paper_1411_5283_gb300/csrc/auto.cu": "19ced58c997d",
                                 "paper_1411_5283_gb300/csrc/common.cuh": "401ac195dfb3",
                                 "paper_1411_5283_gb300/csrc/block_scan.cuh": "8b681f3332d2"}},
 }

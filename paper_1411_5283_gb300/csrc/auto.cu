@@ -41,9 +41,10 @@
 //                          LSD radix passes only past the split area), sort
 //                          longer keys with a bitonic network, and write the
 //                          final records and permutation at the segment's
-//                          output base; a segment larger than shared memory
-//                          (only after a retry) is sorted in chunks and merged
-//                          in global memory
+//                          output base (or, for the packed calls, each word's
+//                          bytes and offset in the §3.1 form); a segment larger
+//                          than shared memory (only after a retry) is sorted in
+//                          chunks and merged in global memory
 #include <type_traits>
 
 #include "block_scan.cuh"
