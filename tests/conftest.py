@@ -36,13 +36,13 @@ def load_golden():
                     continue
                 k, _, v = line.partition("=")
                 k, v = k.strip(), v.strip()
-                if k == "text":
+                if k in ("text", "packed"):
                     d[k] = ast.literal_eval(v)
                 elif k in ("W", "status"):
                     d[k] = int(v)
                 elif k == "words":
                     d[k] = [w.encode() for w in v.split()]
-                elif k == "perm":
+                elif k in ("perm", "offsets"):
                     d[k] = [int(x) for x in v.split()]
                 elif k in ("counts", "swaps"):
                     d[k] = {int(a): int(b) for a, b in (p.split(":") for p in v.split())}

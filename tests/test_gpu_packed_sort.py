@@ -139,3 +139,25 @@ def test_records_packed_size_limits(env):
         with pytest.raises(bs.BsortError) as e:
             bs.bsort_sort_records_packed(d, d, n, W, "auto", None, d, 64, d, d, d, ws, ws_bytes)
         assert e.value.status == bs._lib.E_CAPACITY
+
+
+@pytest.mark.parametrize("alg", ["auto", "merge", "odd_even"])
+def test_text_packed_hand_worked_examples(env, alg):
+    """The hand-worked examples whose packed form is written out in
+    tests/golden (§3.1), through the one-call packed text path."""
+    torch, bs, orc = env
+    from conftest import load_golden
+    cases = [c for c in load_golden() if "packed" in c]
+    assert cases
+    for case in cases:
+        text = case["text"]
+        s = bs.Sorter(len(text) // 2 + 1, case["W"])
+        b, offsets, perm, off, nw = s.sort_text_packed(
+            to_dev(np.frombuffer(text, np.uint8), torch), alg=alg)
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        n = int(nw.item())
+        assert n == len(case["perm"])
+        assert u32(offsets[:n + 1]).tolist() == case["offsets"], case["name"]
+        assert bytes(b[:case["offsets"][-1]].cpu().numpy()) == case["packed"], case["name"]
+        assert u32(perm[:n]).tolist() == case["perm"], case["name"]

@@ -86,6 +86,10 @@ def test_golden(orc, case, method):
     assert counts == case["counts"]
     if "swaps" in case and method == "bubble":
         assert {L: int(res.swaps[L]) for L in range(1, W + 1) if res.swaps[L]} == case["swaps"]
+    if "packed" in case:
+        b, offsets = orc.pack_words(res.out_rec, w.len[res.out_perm])
+        assert bytes(b) == case["packed"]
+        assert offsets.tolist() == case["offsets"]
 
 
 # --------------------------------------------------------------------------
